@@ -1,0 +1,116 @@
+/*
+ * tcfft -- batched 1D and 2D complex-to-complex FP16 FFTs on GB300 (sm_103a)
+ * tensor cores.  C ABI of the library libtcfft.so.
+ *
+ * Method: arXiv 2104.11471 ("tcFFT: Accelerating Half-Precision FFT through
+ * Tensor Cores").  Every radix-16 merging process of the Cooley-Tukey
+ * recursion, Eq. (dft_mm) of Sec. 2.1, X_out = F_16 . (T (.) X_in), runs as a
+ * dense matrix multiply on the 5th-generation tensor cores; radix 2/4/8 steps
+ * run on CUDA cores (Sec. 3.1); the plan / execution-function split follows
+ * Sec. 3.1 ("Architecture", Fig. 1).
+ *
+ * Conventions shared by every call:
+ *  - Transform: forward, X[k] = sum_n x[n] exp(-2 pi i n k / N), sign -,
+ *    no normalisation (Eq. dft_def, Sec. 2.1).  Output in natural order.
+ *  - Data: interleaved complex FP16 (re, im), 4 bytes per point.  1D
+ *    transform b starts at element b*n; 2D data is [batch][nx][ny], row-major
+ *    with ny contiguous (the tcfftPlan2D statement in Sec. 3.1).
+ *  - Split precision (TCFFT_FP16_SPLIT): one buffer holding two planes laid
+ *    out like the plain data, plane 0 = hi, plane 1 = lo; the value is
+ *    hi + lo * 2^-11.  A caller with plain FP16 input passes lo = 0.
+ *  - Device pointers must be 16-byte aligned.  in == out (in place) is
+ *    allowed; otherwise in is never written.
+ *  - Sizes: n, nx, ny powers of two with 16 <= n <= 2^24 (1D) and
+ *    16 <= nx, ny <= 8192 (2D); batch >= 1.  Anything else returns
+ *    TCFFT_ERR_INVALID_SIZE.
+ *  - Errors: every call returns a status code and never aborts.  tcfft_exec
+ *    is asynchronous on the given stream; a device-side failure (a bounded
+ *    wait that expired) is recorded in a plan-owned status word read by
+ *    tcfft_plan_last_error after the stream has been synchronised.
+ *  - Threading: a plan owns scratch memory; do not run two tcfft_exec calls
+ *    on one plan concurrently.  Create one plan per stream.
+ */
+#ifndef TCFFT_H_
+#define TCFFT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tcfft_plan_s* tcfft_plan;
+
+typedef enum {
+  TCFFT_OK = 0,
+  TCFFT_ERR_INVALID_SIZE = 1,     /* unsupported n, nx, ny or batch */
+  TCFFT_ERR_INVALID_VALUE = 2,    /* null or misaligned pointer, bad enum */
+  TCFFT_ERR_ALLOC = 3,            /* device or host allocation failed */
+  TCFFT_ERR_LAUNCH = 4,           /* kernel launch failed */
+  TCFFT_ERR_TIMEOUT = 5,          /* a device-side bounded wait expired */
+  TCFFT_ERR_UNSUPPORTED = 6,      /* no sm_103a device, or feature not built */
+  TCFFT_ERR_NOT_IMPLEMENTED = 7,
+  TCFFT_ERR_CUDA = 8              /* other CUDA runtime error */
+} tcfft_status;
+
+typedef enum {
+  TCFFT_FP16 = 0,       /* FP16 storage and operands, FP32 accumulation */
+  TCFFT_FP16_SPLIT = 1  /* hi + 2^-11 lo pairs, three MMA products per stage */
+} tcfft_precision;
+
+/* Plan a batch of `batch` 1D transforms of length n (the paper's
+ * tcfftPlan1D(plan, nx, batch), Sec. 3.1).  Allocates device twiddle tables
+ * and, for n > 16384, a workspace of batch*n*4 bytes (x2 for split).  On
+ * success *plan owns them until tcfft_destroy.  Not timed by benchmarks. */
+tcfft_status tcfft_plan_1d(tcfft_plan* plan, int64_t n, int64_t batch);
+
+/* Plan a batch of 2D transforms of nx x ny points, row-major, ny contiguous
+ * (the paper's tcfftPlan2D(plan, nx, ny, batch), Sec. 3.1). */
+tcfft_status tcfft_plan_2d(tcfft_plan* plan, int64_t nx, int64_t ny, int64_t batch);
+
+/* As above with an explicit precision; flags must be 0 (reserved). */
+tcfft_status tcfft_plan_1d_ex(tcfft_plan* plan, int64_t n, int64_t batch,
+                              tcfft_precision precision, unsigned flags);
+tcfft_status tcfft_plan_2d_ex(tcfft_plan* plan, int64_t nx, int64_t ny, int64_t batch,
+                              tcfft_precision precision, unsigned flags);
+
+/* The execution function (Sec. 3.1, Fig. 1): runs the plan's merging
+ * kernels in turn on `stream` (a cudaStream_t; NULL = legacy default
+ * stream).  in/out: device buffers of tcfft_io_bytes(plan) bytes each,
+ * 16-byte aligned; may be equal.  Asynchronous: returns once the kernels
+ * are enqueued. */
+tcfft_status tcfft_exec(tcfft_plan plan, const void* in, void* out, void* stream);
+
+/* End-to-end variant for host buffers: copies host_in to a plan-owned
+ * device buffer, runs tcfft_exec, copies the result to host_out, all on
+ * `stream`, and synchronises the stream before returning.  host_in and
+ * host_out hold tcfft_io_bytes(plan) bytes each (pinned memory gives full
+ * copy bandwidth).  The device buffers are allocated on the first call. */
+tcfft_status tcfft_exec_host(tcfft_plan plan, const void* host_in, void* host_out, void* stream);
+
+/* Frees everything the plan owns.  NULL is accepted. */
+tcfft_status tcfft_destroy(tcfft_plan plan);
+
+/* Reads and clears the plan's device status word (synchronises the device
+ * first).  TCFFT_OK when no kernel reported an error. */
+tcfft_status tcfft_plan_last_error(tcfft_plan plan);
+
+/* Bytes of one input (== output) buffer of the plan. */
+size_t tcfft_io_bytes(tcfft_plan plan);
+
+/* Device memory the plan holds besides the caller's buffers (workspace,
+ * tables, host-path staging); for admission control. */
+size_t tcfft_workspace_bytes(tcfft_plan plan);
+
+/* Number of kernel launches one tcfft_exec issues. */
+int tcfft_plan_num_launches(tcfft_plan plan);
+
+/* Human-readable name of a status code (static string). */
+const char* tcfft_status_string(tcfft_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TCFFT_H_ */

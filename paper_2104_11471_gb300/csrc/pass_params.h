@@ -1,0 +1,59 @@
+// Parameters of one "pass": a batch of DFTs of one length N = R * 16^S that a
+// single kernel launch computes entirely on chip (shared memory + TMEM).
+// Host code (planner) and device code (pass kernel) both include this file.
+#pragma once
+#include <cstdint>
+
+namespace tcfft {
+
+// Transform t of a pass is split into three index levels
+//   t1 = t & (I1 - 1), t2 = (t >> log2I1) & (I2 - 1), t3 = t >> (log2I1 + log2I2)
+// and its first element sits at t1*s1 + t2*s2 + t3*s3 (complex elements).
+// Element e of the transform sits at first + e*es.  A side is "contiguous"
+// when es == 1; otherwise it is "strided", and the CTA's group of C
+// transforms must be C consecutive t1 values with s1 == 1, so that every
+// element index reads or writes one run of C adjacent complex values.
+struct SideLayout {
+  int64_t s1, s2, s3, es;
+};
+
+struct PassParams {
+  const uint32_t* in;   // interleaved FP16 complex (re in low half)
+  uint32_t* out;
+  int64_t in_plane;     // split precision: element offset of the lo plane
+  int64_t out_plane;
+  int S;                // radix-16 stages (1..3)
+  int R;                // leading radix on CUDA cores (1, 2, 4, 8)
+  int log2N;            // N = R * 16^S
+  int C;                // transforms per CTA
+  int tiles;            // 128-butterfly MMA tiles per stage = C*N/2048
+  int tmem_cols;        // TMEM columns allocated per CTA
+  int64_t T;            // transforms in the pass
+  int log2I1, log2I2;
+  SideLayout in_l, out_l;
+  int in_contig, out_contig;
+  // W_N table for this pass (factored: W_N^a = hi[a >> log2S] * lo[a & (S-1)])
+  const float* tw_lo;   // float2 pairs
+  const float* tw_hi;
+  int tw_log2S;
+  // optional output twiddle W_M^{col * k} of a multi-pass transform; col is
+  // t1 (level 1) or t2 (level 2) of the transform, k its output index.
+  int otw_level;        // 0 = none
+  int otw_log2M;
+  int otw_log2S;
+  const float* otw_lo;
+  const float* otw_hi;
+  const uint16_t* dft_b;  // radix-16 DFT matrix image(s) in the MMA B layout
+  int* status;            // device error word (0 = ok)
+};
+
+constexpr int kTileRows = 128;        // butterflies per MMA tile (M)
+constexpr int kTileBytes = 8192;      // one tile of A: 128 rows x 32 halves
+constexpr int kBImageBytes = 2048;    // 32 x 32 halves, K-major, no swizzle
+constexpr int kThreads = 128;
+constexpr long long kWaitLimitCycles = 2000000000LL;  // ~1 s at 2 GHz
+
+// Device status codes written by kernels (mirror tcfft_status values).
+constexpr int kDevErrTimeout = 5;
+
+}  // namespace tcfft

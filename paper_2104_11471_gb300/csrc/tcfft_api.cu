@@ -1,0 +1,499 @@
+// C ABI of libtcfft: plans, the execution function, twiddle generation.
+//
+// A plan (Sec. 3.1, "Architecture") is the list of merging-kernel launches
+// ("passes") that together compute the requested transform:
+//  * 1D, n <= single-pass limit: one fused pass (all radix-16 stages of the
+//    transform in one CTA, Sec. 3.2 "Combine multiple mergings").
+//  * 1D, larger n: n = N1 N2, two passes exchanging data through global
+//    memory (Sec. 3.2: "data exchanges between blocks ... can only be done
+//    through global memory").  Pass 1: N1-point DFTs of the strided columns
+//    x[N2 n1 + n2], times W_n^{n2 k1}, into a workspace; pass 2: N2-point
+//    DFTs of the workspace rows, written to X[k1 + N1 k2].
+//  * 2D (Sec. 3.1, "Support batched FFT and 2D FFT"): a pass over the rows
+//    (length ny, contiguous), then a pass over the columns (length nx,
+//    stride ny), the latter split in two passes as above for large nx.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "../../include/tcfft.h"
+#include "pass_params.h"
+
+namespace tcfft {
+cudaError_t launch_pass(const PassParams& p, bool split, dim3 grid, size_t smem, cudaStream_t s);
+cudaError_t configure_pass_kernel(bool split, size_t smem);
+}  // namespace tcfft
+
+using namespace tcfft;
+
+namespace {
+
+constexpr int64_t kMaxLog2_1D = 24;
+constexpr int64_t kMaxLog2_2D = 13;
+
+// points per CTA (C * N) limits: shared memory holds 4 B (plain) or 8 B
+// (split) per point and TMEM 32 (plain) or 64 (split) FP32 columns per 2048.
+constexpr int64_t kCapPlain = 32768;
+constexpr int64_t kCapSplit = 16384;
+// largest single-pass transform (contiguous side)
+constexpr int64_t kSinglePlain = 16384;
+constexpr int64_t kSingleSplit = 8192;
+
+enum Buf { BUF_IN = 0, BUF_OUT = 1, BUF_WS = 2 };
+
+struct TwTable {
+  float* lo = nullptr;
+  float* hi = nullptr;
+  int log2S = 0;
+};
+
+struct Pass {
+  PassParams p;
+  Buf src, dst;
+  dim3 grid;
+  size_t smem;
+};
+
+// ------------------------------------------------------------- device code
+// W_M^m = exp(-2 pi i m / M) in FP64 (sincospi), rounded once to FP32.
+__global__ void twiddle_table_kernel(float2* lo, float2* hi, int log2M, int log2S) {
+  const int64_t S = int64_t(1) << log2S;
+  const int64_t H = int64_t(1) << (log2M - log2S);
+  const int64_t M = int64_t(1) << log2M;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S + H;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t m = (i < S) ? i : (i - S) * S;  // exponent
+    double s, c;
+    sincospi(-2.0 * (double)m / (double)M, &s, &c);
+    const float2 w = make_float2((float)c, (float)s);
+    if (i < S) lo[i] = w; else hi[i - S] = w;
+  }
+}
+
+// B operand of the radix-16 stage: the real 32 x 32 form of F_16,
+//   B[k][n]: k < 16 -> Re of input k, k >= 16 -> Im of input k-16;
+//            n < 16 -> Re of output n, n >= 16 -> Im of output n-16;
+//   [[Re W, Im W], [-Im W, Re W]] with W = W_16^{l m}.
+// Stored K-major without swizzle: core matrices of 8 (n) x 8 (k) halves,
+// K-groups 128 B apart, N-groups 512 B apart.  Image 1 (split only) holds the
+// low part fp16((v - hi) * 2^11).
+__global__ void dft_b_kernel(__half* img) {
+  const int idx = threadIdx.x;  // 1024 threads: one per (k, n)
+  const int k = idx >> 5, n = idx & 31;
+  const int m = k & 15, l = n & 15;
+  double s, c;
+  sincospi(-2.0 * (double)((l * m) & 15) / 16.0, &s, &c);  // W = c + i s
+  double v;
+  if (k < 16) v = (n < 16) ? c : s;
+  else v = (n < 16) ? -s : c;
+  const int off = (n >> 3) * 256 + (k >> 3) * 64 + (n & 7) * 8 + (k & 7);  // in halves
+  const __half h = __double2half(v);
+  img[off] = h;
+  img[1024 + off] = __float2half_rn((float)((v - (double)__half2float(h)) * 2048.0));
+}
+
+// ------------------------------------------------------------- helpers
+int ilog2(int64_t v) {
+  int r = 0;
+  while ((int64_t(1) << r) < v) ++r;
+  return r;
+}
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+tcfft_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return TCFFT_OK;
+  if (e == cudaErrorMemoryAllocation) return TCFFT_ERR_ALLOC;
+  return TCFFT_ERR_CUDA;
+}
+
+}  // namespace
+
+struct tcfft_plan_s {
+  int dims = 1;
+  int64_t n = 0, nx = 0, ny = 0, batch = 0;
+  bool split = false;
+  int64_t points = 0;  // total complex points per plane
+  std::vector<Pass> passes;
+  std::map<int, TwTable> tables;
+  __half* dft_b = nullptr;
+  int* d_status = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  void* h_in_dev = nullptr;
+  void* h_out_dev = nullptr;
+  size_t table_bytes = 0;
+
+  ~tcfft_plan_s() {
+    for (auto& kv : tables) {
+      cudaFree(kv.second.lo);
+      cudaFree(kv.second.hi);
+    }
+    cudaFree(dft_b);
+    cudaFree(d_status);
+    cudaFree(ws);
+    cudaFree(h_in_dev);
+    cudaFree(h_out_dev);
+  }
+
+  size_t io_bytes() const { return (size_t)points * 4u * (split ? 2u : 1u); }
+
+  tcfft_status table(int log2M, TwTable** out) {
+    auto it = tables.find(log2M);
+    if (it != tables.end()) {
+      *out = &it->second;
+      return TCFFT_OK;
+    }
+    TwTable t;
+    t.log2S = (log2M + 1) / 2;
+    const int64_t S = int64_t(1) << t.log2S, H = int64_t(1) << (log2M - t.log2S);
+    if (cudaMalloc(&t.lo, S * 8) != cudaSuccess) return TCFFT_ERR_ALLOC;
+    if (cudaMalloc(&t.hi, H * 8) != cudaSuccess) {
+      cudaFree(t.lo);
+      return TCFFT_ERR_ALLOC;
+    }
+    table_bytes += (size_t)(S + H) * 8;
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((S + H + threads - 1) / threads, 1024);
+    twiddle_table_kernel<<<blocks, threads>>>((float2*)t.lo, (float2*)t.hi, log2M, t.log2S);
+    if (cudaGetLastError() != cudaSuccess) return TCFFT_ERR_LAUNCH;
+    tables[log2M] = t;
+    *out = &tables[log2M];
+    return TCFFT_OK;
+  }
+};
+
+namespace {
+
+// Describes one side (input or output) of a pass over a set of transforms.
+struct Side {
+  int64_t s1, s2, s3, es;
+};
+
+// Adds one fused pass computing DFTs of length L on T transforms indexed by
+// (t1 < I1, t2 < I2, t3), reading `src` with layout `in` and writing `dst`
+// with layout `out`.  otw_level / log2M: optional output twiddle W_M^{col k}.
+tcfft_status add_pass(tcfft_plan_s* pl, int64_t L, int64_t T, int64_t I1, int64_t I2, Side in,
+                      Side out, Buf src, Buf dst, int otw_level, int log2M) {
+  Pass ps;
+  std::memset(&ps.p, 0, sizeof(ps.p));
+  PassParams& p = ps.p;
+  const int log2L = ilog2(L);
+  p.S = log2L / 4;
+  p.R = 1 << (log2L % 4);
+  p.log2N = log2L;
+  if (p.S < 1) return TCFFT_ERR_INVALID_SIZE;
+  const bool in_contig = in.es == 1, out_contig = out.es == 1;
+  const int64_t cap = pl->split ? kCapSplit : kCapPlain;
+  int64_t C;
+  if (in_contig && out_contig) {
+    const int64_t target = pl->split ? 4096 : 8192;
+    C = std::max<int64_t>(1, target / L);
+    if (C * L > cap) return TCFFT_ERR_INVALID_SIZE;
+  } else {
+    // strided side: C adjacent transforms per element index, C | I1, C >= 8
+    const int64_t soft = pl->split ? 8192 : 16384;
+    C = 0;
+    for (int64_t c : {32, 16, 8}) {
+      if (I1 % c == 0 && c * L <= soft) {
+        C = c;
+        break;
+      }
+    }
+    if (C == 0 && I1 % 8 == 0 && 8 * L <= cap) C = 8;
+    if (C == 0) return TCFFT_ERR_INVALID_SIZE;
+    // bring small transforms up to at least one full MMA tile when possible
+    while (C * L < 2048 && I1 % (2 * C) == 0 && 2 * C * L <= cap) C *= 2;
+    if ((in.s1 != 1 && !in_contig) || (out.s1 != 1 && !out_contig)) return TCFFT_ERR_INVALID_SIZE;
+  }
+  const int64_t P = C * L;
+  p.C = (int)C;
+  p.tiles = (int)((P + 2047) / 2048);
+  const int planes = pl->split ? 2 : 1;
+  int cols = 32;
+  while (cols < 32 * p.tiles * planes) cols *= 2;
+  if (cols > 512) return TCFFT_ERR_INVALID_SIZE;
+  p.tmem_cols = cols;
+  p.T = T;
+  p.log2I1 = ilog2(I1);
+  p.log2I2 = ilog2(I2);
+  p.in_l = SideLayout{in.s1, in.s2, in.s3, in.es};
+  p.out_l = SideLayout{out.s1, out.s2, out.s3, out.es};
+  p.in_contig = in_contig;
+  p.out_contig = out_contig;
+  TwTable* tw = nullptr;
+  tcfft_status st = pl->table(log2L, &tw);
+  if (st != TCFFT_OK) return st;
+  p.tw_lo = tw->lo;
+  p.tw_hi = tw->hi;
+  p.tw_log2S = tw->log2S;
+  p.otw_level = otw_level;
+  if (otw_level) {
+    TwTable* ot = nullptr;
+    st = pl->table(log2M, &ot);
+    if (st != TCFFT_OK) return st;
+    p.otw_log2M = log2M;
+    p.otw_log2S = ot->log2S;
+    p.otw_lo = ot->lo;
+    p.otw_hi = ot->hi;
+  }
+  p.dft_b = reinterpret_cast<const uint16_t*>(pl->dft_b);
+  p.status = pl->d_status;
+  p.in_plane = pl->points;
+  p.out_plane = pl->points;
+  ps.src = src;
+  ps.dst = dst;
+  ps.grid = dim3((unsigned)((T + C - 1) / C));
+  // shared memory: A tiles (x planes), B image(s), barrier words, 1 KB alignment slack;
+  // padded so that shared memory, not TMEM allocation, limits CTAs per SM.
+  size_t smem = 1024 + (size_t)planes * p.tiles * kTileBytes + (size_t)planes * kBImageBytes + 64;
+  const int ctas_tmem = 512 / cols;
+  const size_t sm_total = 228 * 1024;
+  const size_t per_cta_max = sm_total / ctas_tmem - 1024;
+  if (smem < per_cta_max) smem = std::min<size_t>(per_cta_max, 227 * 1024);
+  if (smem > 227 * 1024) return TCFFT_ERR_INVALID_SIZE;
+  ps.smem = smem;
+  pl->passes.push_back(ps);
+  return TCFFT_OK;
+}
+
+constexpr int64_t kNoLevel = int64_t(1) << 40;  // "unbounded" index level
+
+tcfft_status plan_1d(tcfft_plan_s* pl) {
+  const int64_t n = pl->n, B = pl->batch;
+  const int64_t single = pl->split ? kSingleSplit : kSinglePlain;
+  if (n <= single) {
+    Side s{n, 0, 0, 1};
+    return add_pass(pl, n, B, kNoLevel, 1, s, s, BUF_IN, BUF_OUT, 0, 0);
+  }
+  const int lg = ilog2(n);
+  const int64_t N1 = int64_t(1) << ((lg + 1) / 2), N2 = n / N1;
+  pl->ws_bytes = (size_t)B * n * 4 * (pl->split ? 2 : 1);
+  if (cudaMalloc(&pl->ws, pl->ws_bytes) != cudaSuccess) {
+    pl->ws = nullptr;
+    return TCFFT_ERR_ALLOC;
+  }
+  // pass 1: columns n2 of length N1 (stride N2), times W_n^{n2 k1}
+  Side c1{1, n, 0, N2};
+  tcfft_status st = add_pass(pl, N1, B * N2, N2, kNoLevel, c1, c1, BUF_IN, BUF_WS, 1, lg);
+  if (st != TCFFT_OK) return st;
+  // pass 2: rows k1 of length N2, written to X[k1 + N1 k2]
+  Side in2{N2, n, 0, 1}, out2{1, n, 0, N1};
+  return add_pass(pl, N2, B * N1, N1, kNoLevel, in2, out2, BUF_WS, BUF_OUT, 0, 0);
+}
+
+tcfft_status plan_2d(tcfft_plan_s* pl) {
+  const int64_t nx = pl->nx, ny = pl->ny, B = pl->batch;
+  const int64_t mat = nx * ny;
+  // rows: nx * B transforms of length ny, contiguous
+  Side r{ny, 0, 0, 1};
+  tcfft_status st = add_pass(pl, ny, B * nx, kNoLevel, 1, r, r, BUF_IN, BUF_OUT, 0, 0);
+  if (st != TCFFT_OK) return st;
+  const int64_t cap = pl->split ? kCapSplit : kCapPlain;
+  if (8 * nx <= cap) {
+    // columns: ny * B transforms of length nx, stride ny, in place on out
+    Side c{1, mat, 0, ny};
+    return add_pass(pl, nx, B * ny, ny, kNoLevel, c, c, BUF_OUT, BUF_OUT, 0, 0);
+  }
+  // columns too long for one CTA group: nx = N1 N2 in two passes
+  const int lg = ilog2(nx);
+  const int64_t N1 = int64_t(1) << ((lg + 1) / 2), N2 = nx / N1;
+  pl->ws_bytes = (size_t)B * mat * 4 * (pl->split ? 2 : 1);
+  if (cudaMalloc(&pl->ws, pl->ws_bytes) != cudaSuccess) {
+    pl->ws = nullptr;
+    return TCFFT_ERR_ALLOC;
+  }
+  // pass A: element n1 of column (iy, n2) at (N2 n1 + n2) ny + iy
+  Side a{1, ny, mat, N2 * ny};
+  st = add_pass(pl, N1, B * ny * N2, ny, N2, a, a, BUF_OUT, BUF_WS, 2, lg);
+  if (st != TCFFT_OK) return st;
+  // pass B: row k1 (elements n2 at (N2 k1 + n2) ny + iy) -> X[k1 + N1 k2]
+  Side bi{1, N2 * ny, mat, ny}, bo{1, ny, mat, N1 * ny};
+  return add_pass(pl, N2, B * ny * N1, ny, N1, bi, bo, BUF_WS, BUF_OUT, 0, 0);
+}
+
+tcfft_status check_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TCFFT_ERR_UNSUPPORTED;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return TCFFT_ERR_UNSUPPORTED;
+  if (prop.major != 10 || prop.minor != 3) return TCFFT_ERR_UNSUPPORTED;
+  return TCFFT_OK;
+}
+
+tcfft_status common_init(tcfft_plan_s* pl) {
+  if (configure_pass_kernel(pl->split, 227 * 1024) != cudaSuccess) return TCFFT_ERR_CUDA;
+  if (cudaMalloc(&pl->d_status, sizeof(int)) != cudaSuccess) return TCFFT_ERR_ALLOC;
+  if (cudaMemset(pl->d_status, 0, sizeof(int)) != cudaSuccess) return TCFFT_ERR_CUDA;
+  if (cudaMalloc(&pl->dft_b, 2 * kBImageBytes) != cudaSuccess) return TCFFT_ERR_ALLOC;
+  dft_b_kernel<<<1, 1024>>>(pl->dft_b);
+  if (cudaGetLastError() != cudaSuccess) return TCFFT_ERR_LAUNCH;
+  return TCFFT_OK;
+}
+
+tcfft_status finish(tcfft_plan_s* pl, tcfft_status st, tcfft_plan* out) {
+  if (st == TCFFT_OK) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) st = from_cuda(e);
+  }
+  if (st != TCFFT_OK) {
+    delete pl;
+    *out = nullptr;
+    return st;
+  }
+  *out = pl;
+  return TCFFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tcfft_status tcfft_plan_1d_ex(tcfft_plan* plan, int64_t n, int64_t batch, tcfft_precision precision,
+                              unsigned flags) {
+  if (!plan) return TCFFT_ERR_INVALID_VALUE;
+  *plan = nullptr;
+  if (flags != 0 || (precision != TCFFT_FP16 && precision != TCFFT_FP16_SPLIT))
+    return TCFFT_ERR_INVALID_VALUE;
+  if (!is_pow2(n) || n < 16 || ilog2(n) > kMaxLog2_1D || batch < 1) return TCFFT_ERR_INVALID_SIZE;
+  if (precision == TCFFT_FP16_SPLIT && ilog2(n) > 22) return TCFFT_ERR_INVALID_SIZE;
+  if (batch > (int64_t(1) << 40) / n) return TCFFT_ERR_INVALID_SIZE;
+  tcfft_status st = check_device();
+  if (st != TCFFT_OK) return st;
+  tcfft_plan_s* pl = new (std::nothrow) tcfft_plan_s();
+  if (!pl) return TCFFT_ERR_ALLOC;
+  pl->dims = 1;
+  pl->n = n;
+  pl->batch = batch;
+  pl->split = precision == TCFFT_FP16_SPLIT;
+  pl->points = n * batch;
+  st = common_init(pl);
+  if (st == TCFFT_OK) st = plan_1d(pl);
+  return finish(pl, st, plan);
+}
+
+tcfft_status tcfft_plan_1d(tcfft_plan* plan, int64_t n, int64_t batch) {
+  return tcfft_plan_1d_ex(plan, n, batch, TCFFT_FP16, 0);
+}
+
+tcfft_status tcfft_plan_2d_ex(tcfft_plan* plan, int64_t nx, int64_t ny, int64_t batch,
+                              tcfft_precision precision, unsigned flags) {
+  if (!plan) return TCFFT_ERR_INVALID_VALUE;
+  *plan = nullptr;
+  if (flags != 0 || (precision != TCFFT_FP16 && precision != TCFFT_FP16_SPLIT))
+    return TCFFT_ERR_INVALID_VALUE;
+  if (!is_pow2(nx) || !is_pow2(ny) || nx < 16 || ny < 16 || ilog2(nx) > kMaxLog2_2D ||
+      ilog2(ny) > kMaxLog2_2D || batch < 1)
+    return TCFFT_ERR_INVALID_SIZE;
+  if (batch > (int64_t(1) << 40) / (nx * ny)) return TCFFT_ERR_INVALID_SIZE;
+  tcfft_status st = check_device();
+  if (st != TCFFT_OK) return st;
+  tcfft_plan_s* pl = new (std::nothrow) tcfft_plan_s();
+  if (!pl) return TCFFT_ERR_ALLOC;
+  pl->dims = 2;
+  pl->nx = nx;
+  pl->ny = ny;
+  pl->batch = batch;
+  pl->split = precision == TCFFT_FP16_SPLIT;
+  pl->points = nx * ny * batch;
+  st = common_init(pl);
+  if (st == TCFFT_OK) st = plan_2d(pl);
+  return finish(pl, st, plan);
+}
+
+tcfft_status tcfft_plan_2d(tcfft_plan* plan, int64_t nx, int64_t ny, int64_t batch) {
+  return tcfft_plan_2d_ex(plan, nx, ny, batch, TCFFT_FP16, 0);
+}
+
+tcfft_status tcfft_exec(tcfft_plan plan, const void* in, void* out, void* stream) {
+  if (!plan || !in || !out) return TCFFT_ERR_INVALID_VALUE;
+  if ((reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(out) & 15))
+    return TCFFT_ERR_INVALID_VALUE;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (const Pass& ps : plan->passes) {
+    PassParams p = ps.p;
+    void* bufs[3] = {const_cast<void*>(in), out, plan->ws};
+    p.in = reinterpret_cast<const uint32_t*>(bufs[ps.src]);
+    p.out = reinterpret_cast<uint32_t*>(bufs[ps.dst]);
+    cudaError_t e = launch_pass(p, plan->split, ps.grid, ps.smem, s);
+    if (e != cudaSuccess) return TCFFT_ERR_LAUNCH;
+  }
+  return TCFFT_OK;
+}
+
+tcfft_status tcfft_exec_host(tcfft_plan plan, const void* host_in, void* host_out, void* stream) {
+  if (!plan || !host_in || !host_out) return TCFFT_ERR_INVALID_VALUE;
+  const size_t bytes = plan->io_bytes();
+  if (!plan->h_in_dev) {
+    if (cudaMalloc(&plan->h_in_dev, bytes) != cudaSuccess) {
+      plan->h_in_dev = nullptr;
+      return TCFFT_ERR_ALLOC;
+    }
+    if (cudaMalloc(&plan->h_out_dev, bytes) != cudaSuccess) {
+      cudaFree(plan->h_in_dev);
+      plan->h_in_dev = nullptr;
+      plan->h_out_dev = nullptr;
+      return TCFFT_ERR_ALLOC;
+    }
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(plan->h_in_dev, host_in, bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return from_cuda(e);
+  tcfft_status st = tcfft_exec(plan, plan->h_in_dev, plan->h_out_dev, stream);
+  if (st != TCFFT_OK) return st;
+  e = cudaMemcpyAsync(host_out, plan->h_out_dev, bytes, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return from_cuda(e);
+  e = cudaStreamSynchronize(s);
+  return from_cuda(e);
+}
+
+tcfft_status tcfft_destroy(tcfft_plan plan) {
+  delete plan;
+  return TCFFT_OK;
+}
+
+tcfft_status tcfft_plan_last_error(tcfft_plan plan) {
+  if (!plan) return TCFFT_ERR_INVALID_VALUE;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return from_cuda(e);
+  int v = 0;
+  e = cudaMemcpy(&v, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return from_cuda(e);
+  cudaMemset(plan->d_status, 0, sizeof(int));
+  return (tcfft_status)v;
+}
+
+size_t tcfft_io_bytes(tcfft_plan plan) { return plan ? plan->io_bytes() : 0; }
+
+size_t tcfft_workspace_bytes(tcfft_plan plan) {
+  if (!plan) return 0;
+  size_t b = plan->ws_bytes + plan->table_bytes + 2 * kBImageBytes + sizeof(int);
+  if (plan->h_in_dev) b += 2 * plan->io_bytes();
+  return b;
+}
+
+int tcfft_plan_num_launches(tcfft_plan plan) { return plan ? (int)plan->passes.size() : 0; }
+
+const char* tcfft_status_string(tcfft_status s) {
+  switch (s) {
+    case TCFFT_OK: return "TCFFT_OK";
+    case TCFFT_ERR_INVALID_SIZE: return "TCFFT_ERR_INVALID_SIZE";
+    case TCFFT_ERR_INVALID_VALUE: return "TCFFT_ERR_INVALID_VALUE";
+    case TCFFT_ERR_ALLOC: return "TCFFT_ERR_ALLOC";
+    case TCFFT_ERR_LAUNCH: return "TCFFT_ERR_LAUNCH";
+    case TCFFT_ERR_TIMEOUT: return "TCFFT_ERR_TIMEOUT";
+    case TCFFT_ERR_UNSUPPORTED: return "TCFFT_ERR_UNSUPPORTED";
+    case TCFFT_ERR_NOT_IMPLEMENTED: return "TCFFT_ERR_NOT_IMPLEMENTED";
+    case TCFFT_ERR_CUDA: return "TCFFT_ERR_CUDA";
+  }
+  return "TCFFT_ERR_UNKNOWN";
+}
+
+}  // extern "C"
