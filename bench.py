@@ -1,0 +1,367 @@
+"""Benchmark: batched FP16 FFT GFLOP/s (5 N log2 N per transform) on GB300.
+
+Default workload (the 1D sweep): N = 2^8, 2^10, ..., 2^24 with batch =
+2^28 / N, so every exec moves 2^28 complex FP16 points (1 GiB in, 1 GiB
+out).  One "step" runs the whole sweep: one tcfft_exec per size, inputs
+already resident in HBM.  Inputs are larger than L2 (1 GiB per exec), so no
+L2 flush is needed between execs.
+
+Printed on rank 0 as ONE JSON line:
+  value      -- whole-job GFLOP/s over all ranks (sum of 5 N log2N * batch
+                over the step, divided by the step time, max over ranks)
+  e2e        -- the same metric through tcfft_exec_host with pinned host
+                buffers (host->device copy, exec, device->host copy timed)
+  roofline   -- algorithmic HBM bytes (8 B per point per exec) / exec time
+                of the pass kernel launches, against the measured copy peak
+  cpu_baseline -- the FP64 CPU oracle on a bounded sample of the workload
+  gpu_launches -- libtcfft kernel launches inside the timed region
+
+--impl reference runs the FP64 CPU oracle (the reference for this method)
+on the host cores instead, each step a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "batched FP16 FFT GFLOP/s (5NlogN) & %HBM peak at stated rel-err; serve p99 latency"
+UNIT = "GFLOP/s"
+POINTS = 1 << 28
+SWEEP = [8, 10, 12, 14, 16, 18, 20, 22, 24]
+
+
+def flops_1d(n: int, batch: int) -> float:
+    return 5.0 * n * math.log2(n) * batch
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle
+_ORACLE_INPUTS = {}
+
+
+def oracle_sample(sizes, budget_points: int):
+    """FP64 oracle on a bounded sample: per size, max(1, budget_points // n)
+    transforms of the size's seeded input.  Returns (flops, seconds, threads, desc)."""
+    import oracle
+    import seeded_inputs as si
+    oracle.build()
+    threads = oracle.default_threads()
+    total_flops, total_s = 0.0, 0.0
+    parts = []
+    for lg in sizes:
+        n = 1 << lg
+        b = max(1, budget_points // n)
+        key = (lg, b)
+        if key not in _ORACLE_INPUTS:
+            _ORACLE_INPUTS[key] = si.as_complex128(si.half_input((b, n), seed=si.sweep_seed(lg)))
+        x = _ORACLE_INPUTS[key]
+        t0 = time.perf_counter()
+        oracle.fft_batch(x, nthreads=threads)
+        total_s += time.perf_counter() - t0
+        total_flops += flops_1d(n, b)
+        parts.append(f"2^{lg}x{b}")
+    return total_flops, total_s, min(threads, os.cpu_count() or 1), " ".join(parts)
+
+
+# ------------------------------------------------------------------ dist
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    budget = args.cpu_sample_points
+    flops, secs, cores, desc = 0.0, 0.0, 1, ""
+    if args.warmup:
+        oracle_sample(SWEEP, budget)  # untimed: builds the oracle, draws the inputs
+    for _ in range(args.steps):
+        f, s, cores, desc = oracle_sample(SWEEP, budget)
+        flops += f
+        secs += s
+    value = flops / secs / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "1d_sweep: N=2^8..2^24 step 2^2, batch=2^28/N, FP16 uniform[-1,1] inputs",
+                   "sample": f"FP64 CPU oracle, per size max(1, {budget}//N) transforms"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_2104_11471_gb300 as tc
+    import seeded_inputs as si
+
+    tc.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    sizes = [int(s) for s in args.sizes.split(",")] if args.sizes else SWEEP
+    plans = []
+    for lg in sizes:
+        n = 1 << lg
+        plans.append((lg, n, POINTS // n, tc.Plan.plan_1d(n, POINTS // n)))
+    # inputs: one seeded FP16 draw of 2^28 points, resident in HBM (1 GiB)
+    rng = np.random.default_rng(1000 + rank)
+    h = rng.uniform(-1.0, 1.0, size=2 * POINTS).astype(np.float16)
+    x = torch.from_numpy(h.view(np.uint16)).to(dev)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    launches_per_step = sum(p.num_launches for *_, p in plans)
+
+    def step(events=None):
+        for i, (lg, n, b, p) in enumerate(plans):
+            if events is not None:
+                events[i][0].record(stream)
+            p.exec(x, y, stream)
+            if events is not None:
+                events[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for *_, p in plans:
+        st = p.last_error()
+        if st != 0:
+            raise RuntimeError(f"device status {st} in warm-up")
+
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in plans] for _ in range(args.steps)]
+    t_start, t_stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clk.start()
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(ev[k])
+    t_stop.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    barrier(world)
+    elapsed_ms = t_start.elapsed_time(t_stop)
+    elapsed_ms = max_over_ranks(elapsed_ms, world)
+    flops_step = sum(flops_1d(n, b) for _, n, b, _ in plans)
+    value = world * flops_step * args.steps / (elapsed_ms / 1e3) / 1e9
+
+    peak, peak_kind = peaks()
+    per_n = []
+    tot_bytes, tot_ms = 0.0, 0.0
+    for i, (lg, n, b, p) in enumerate(plans):
+        ms = [ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps)]
+        avg = sum(ms) / len(ms)
+        alg = 8.0 * n * b
+        tot_bytes += alg
+        tot_ms += avg
+        per_n.append({"n": n, "batch": b, "launches": p.num_launches, "ms": round(avg, 4),
+                      "gflops": round(flops_1d(n, b) / (avg / 1e3) / 1e9, 1),
+                      "alg_gbs": round(alg / (avg / 1e3) / 1e9, 1),
+                      "frac": round(alg / (avg / 1e3) / 1e9 / peak, 4)})
+    achieved = tot_bytes / (tot_ms / 1e3) / 1e9
+    for *_, p in plans:
+        st = p.last_error()
+        if st != 0:
+            raise RuntimeError(f"device status {st} in timed region")
+
+    # end to end: pinned host buffers through tcfft_exec_host
+    e2e = None
+    if not args.no_e2e:
+        hin = torch.from_numpy(h.view(np.uint16)).pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        for *_, p in plans:
+            p.exec_host(hin, hout, stream)  # warm-up (allocates the plan's device buffers)
+        barrier(world)
+        t0 = time.perf_counter()
+        e2e_steps = max(1, min(args.steps, 3))
+        for _ in range(e2e_steps):
+            for *_, p in plans:
+                p.exec_host(hin, hout, stream)
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": world * flops_step * e2e_steps / e2e_s / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": len(plans) * hin.numel() * 2,
+               "d2h_bytes_per_step": len(plans) * hout.numel() * 2}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        f, s, cores, desc = oracle_sample(sizes, args.cpu_sample_points)
+        cpu = {"value": f / s / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"FP64 oracle, same sizes, per size max(1,{args.cpu_sample_points}//N) transforms: {desc}"}
+
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic_1d_sweep.json")
+    if os.path.exists(tpath):
+        try:
+            with open(tpath) as f:
+                td = json.load(f)
+            if td.get("kernel_hash") == kernel_hash():
+                traffic = td.get("traffic_bytes_per_step")
+        except Exception:
+            traffic = None
+    for *_, p in plans:
+        p.destroy()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+        "config": {"workload": "1d_sweep: N=2^8..2^24 step 2^2, batch=2^28/N (1 GiB FP16 per exec), "
+                               "one exec per size per step, uniform[-1,1] seeded inputs",
+                   "sizes": [1 << s for s in sizes], "points_per_exec": POINTS, "precision": "plain FP16",
+                   "l2": "inputs larger than L2 (1 GiB per exec), no flush", "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "kernel": "pass_kernel (all launches of the step; unit = one exec, 8 B/point)",
+                     "peak_kind": peak_kind},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "per_n": per_n,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def kernel_hash() -> str:
+    """Hash of the kernel sources, so stored ncu traffic is dropped once they change."""
+    import hashlib
+    hsh = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2104_11471_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, name), "rb") as f:
+                hsh.update(f.read())
+    return hsh.hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tcfft", choices=["tcfft", "reference"])
+    ap.add_argument("--sizes", default="", help="comma-separated log2 sizes (default: the sweep)")
+    ap.add_argument("--cpu-sample-points", type=int, default=1 << 21)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_gpu(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
