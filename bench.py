@@ -313,7 +313,7 @@ def run_gpu(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
-        "config": {"workload": "1d_sweep: N=2^8..2^24 step 2^2, batch=2^28/N (1 GiB FP16 per exec), "
+        "config": {"workload": f"1d_sweep: N=2^8..2^24 step 2^2, batch=2^{args.log2_points}/N, "
                                "one exec per size per step, uniform[-1,1] seeded inputs",
                    "sizes": [1 << s for s in sizes], "points_per_exec": POINTS, "precision": "plain FP16",
                    "l2": "inputs larger than L2 (1 GiB per exec), no flush", "parallelism": f"replicas x{world}"},
@@ -350,9 +350,13 @@ def main():
     ap.add_argument("--impl", default="tcfft", choices=["tcfft", "reference"])
     ap.add_argument("--sizes", default="", help="comma-separated log2 sizes (default: the sweep)")
     ap.add_argument("--cpu-sample-points", type=int, default=1 << 21)
+    ap.add_argument("--log2-points", type=int, default=28,
+                    help="points per exec (smaller values for profiling captures only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    global POINTS
+    POINTS = 1 << args.log2_points
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)

@@ -11,7 +11,9 @@
 // and stage j repeats this on the length-16^{S-j+1} sub-sequences, so that
 // after stage S the output index is k = k_1 + 16 k_2 + ... + 16^{S-1} k_S.
 // A leading radix-R step (R in {1,2,4,8}, Sec. 3.1 "radix 2 and radix 4 on
-// CUDA cores") splits N = R L the same way before the first radix-16 stage.
+// CUDA cores") splits N = R L the same way before the first radix-16 stage:
+// sub-transform k0 gets y_k0[n'] = W_N^{k0 n'} sum_{n0} x[n0 L + n'] W_R^{n0 k0}
+// and X[k0 + R k'] = DFT_L(y_k0)[k'].
 //
 // GB300 mapping.
 //  * Every radix-16 butterfly column is one row of an MMA A operand:
@@ -31,8 +33,10 @@
 //    fragments, Alg. 2); the 16 factors of one thread are powers of one
 //    base read from a factored FP32 table generated in FP64.
 //  * The final stage writes natural-order results into a swizzled staging
-//    copy of shared memory, which is then stored with 16-byte coalesced
+//    copy in shared memory, which is then stored with 16-byte coalesced
 //    writes ("continuous size", Sec. 4.2, Table gbw).
+//  * Sizes, radices and layouts are template parameters: all index
+//    arithmetic is shifts and masks on 32-bit offsets from per-CTA bases.
 // Split precision (hi + 2^-11 lo, FP32 accumulation, three products per
 // stage) follows the paper's "precision recovery" future work (Sec. 7).
 #pragma once
@@ -43,6 +47,24 @@
 #include "tc_ptx.cuh"
 
 namespace tcfft {
+
+template <int LOG2N_, int MODE, bool SPLIT_>
+struct PassCfg {
+  static constexpr int S = LOG2N_ / 4;         // radix-16 stages
+  static constexpr int LOG2RX = LOG2N_ % 4;     // leading radix on CUDA cores
+  static constexpr int RX = 1 << LOG2RX;
+  static constexpr int LOG2N = LOG2N_;
+  static constexpr int N = 1 << LOG2N;
+  static constexpr int LOG2L = 4 * S;          // radix-16 sub-transform length
+  static constexpr int L = 1 << LOG2L;
+  static constexpr int LOG2LQ = 4 * (S - 1);   // 16^{S-1}
+  static constexpr int LQ = 1 << LOG2LQ;
+  static constexpr bool IN_C = MODE != kModeStrided;
+  static constexpr bool OUT_C = MODE == kModeContig;
+  static constexpr bool SPLIT = SPLIT_;
+  static constexpr int PLANES = SPLIT ? 2 : 1;
+  static_assert(S >= 1 && S <= 3, "pass length out of range");
+};
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -58,13 +80,6 @@ __device__ __forceinline__ uint32_t a_off(uint32_t m, uint32_t k) {
          ((((mm & 63u) >> 3) ^ (k & 7u)) << 4) + ((mm & 7u) << 1);
 }
 
-// Staging buffer word (one complex = 4 bytes) with a 16-byte-chunk XOR
-// swizzle inside each 128-byte line.
-__device__ __forceinline__ uint32_t stg_word(uint32_t idx) {
-  const uint32_t q = idx >> 2;
-  return ((q ^ ((q >> 3) & 7u)) << 2) | (idx & 3u);
-}
-
 __device__ __forceinline__ int64_t side_base(const SideLayout& l, int64_t t, int log2I1,
                                              int log2I2) {
   const int64_t t1 = t & ((int64_t(1) << log2I1) - 1);
@@ -74,11 +89,11 @@ __device__ __forceinline__ int64_t side_base(const SideLayout& l, int64_t t, int
   return t1 * l.s1 + t2 * l.s2 + t3 * l.s3;
 }
 
-__device__ __forceinline__ float2 tw_lookup(const float* lo, const float* hi, uint64_t a,
+__device__ __forceinline__ float2 tw_lookup(const float* lo, const float* hi, uint32_t a,
                                             int log2M, int log2S) {
-  a &= (uint64_t(1) << log2M) - 1;
+  a &= (1u << log2M) - 1u;
   const float2 h = __ldg(reinterpret_cast<const float2*>(hi) + (a >> log2S));
-  const float2 l = __ldg(reinterpret_cast<const float2*>(lo) + (a & ((uint64_t(1) << log2S) - 1)));
+  const float2 l = __ldg(reinterpret_cast<const float2*>(lo) + (a & ((1u << log2S) - 1u)));
   return cmulf(h, l);
 }
 
@@ -90,9 +105,10 @@ __device__ __forceinline__ uint32_t f2h2(float a, float b) {
   __half2 h = __floats2half2_rn(a, b);
   return *reinterpret_cast<uint32_t*>(&h);
 }
-__device__ __forceinline__ uint32_t f2h1(float a) {
-  __half h = __float2half_rn(a);
-  return (uint32_t)(*reinterpret_cast<uint16_t*>(&h));
+// low part of the split pair: fp16((v - fp16(v)) * 2^11), per component
+__device__ __forceinline__ uint32_t split_lo(float a, float b, uint32_t hi) {
+  const float2 hf = h2f(hi);
+  return f2h2((a - hf.x) * 2048.0f, (b - hf.y) * 2048.0f);
 }
 
 // In-place DFT of length RX (1, 2, 4, 8) on FP32 complex values.
@@ -120,8 +136,8 @@ __device__ __forceinline__ void small_dft(float2 (&v)[RX]) {
     small_dft<4>(o);
     const float h = 0.70710678118654752f;
     // W_8^k for k = 0..3: 1, (1-i)/sqrt2, -i, (-1-i)/sqrt2
-    float2 w1 = make_float2(h, -h), w3 = make_float2(-h, -h);
-    float2 t0 = o[0], t1 = cmulf(o[1], w1), t2 = make_float2(o[2].y, -o[2].x), t3 = cmulf(o[3], w3);
+    const float2 t0 = o[0], t1 = cmulf(o[1], make_float2(h, -h)), t2 = make_float2(o[2].y, -o[2].x),
+                 t3 = cmulf(o[3], make_float2(-h, -h));
     v[0] = make_float2(e[0].x + t0.x, e[0].y + t0.y);
     v[4] = make_float2(e[0].x - t0.x, e[0].y - t0.y);
     v[1] = make_float2(e[1].x + t1.x, e[1].y + t1.y);
@@ -133,12 +149,37 @@ __device__ __forceinline__ void small_dft(float2 (&v)[RX]) {
   }
 }
 
-// Writes 8 consecutive butterfly rows (m0 multiple of 8) of input k of A:
-// re halves at K = k, im halves at K = 16 + k.
-__device__ __forceinline__ void a_store8(uint8_t* A, uint32_t m0, uint32_t k, uint4 re8,
-                                         uint4 im8) {
-  *reinterpret_cast<uint4*>(A + a_off(m0, k)) = re8;
-  *reinterpret_cast<uint4*>(A + a_off(m0, 16 + k)) = im8;
+// Writes 8 consecutive butterfly rows (m0 multiple of 8) of input k of A from
+// 8 packed complex values: re halves at K = k, im halves at K = 16 + k.
+__device__ __forceinline__ void a_store8c(uint8_t* A, uint32_t m0, uint32_t k,
+                                          const uint32_t (&v)[8]) {
+  const uint4 re = make_uint4(__byte_perm(v[0], v[1], 0x5410), __byte_perm(v[2], v[3], 0x5410),
+                              __byte_perm(v[4], v[5], 0x5410), __byte_perm(v[6], v[7], 0x5410));
+  const uint4 im = make_uint4(__byte_perm(v[0], v[1], 0x7632), __byte_perm(v[2], v[3], 0x7632),
+                              __byte_perm(v[4], v[5], 0x7632), __byte_perm(v[6], v[7], 0x7632));
+  *reinterpret_cast<uint4*>(A + a_off(m0, k)) = re;
+  *reinterpret_cast<uint4*>(A + a_off(m0, 16 + k)) = im;
+}
+
+// Staging-buffer swizzle for the final stage: the 16-byte chunk index inside
+// each 128-byte line is XORed with a key taken from output-index bits that
+// differ between the lanes of a warp and are constant inside the line, so
+// the single-word writes of one warp spread over the banks while the
+// copy-out still reads whole 16-byte chunks.
+template <class K>
+__device__ __forceinline__ uint32_t stg_key(uint32_t ko, int log2C) {
+  if constexpr (K::OUT_C) {
+    constexpr int KS0 = (K::S >= 2) ? (K::LOG2RX + 4 * (K::S - 2)) : 0;
+    constexpr int KS = KS0 > 5 ? KS0 : 5;  // ko bits >= 5 are constant in a line
+    if constexpr (K::N >= 32) return (ko >> KS) & 7u;
+    return 0u;
+  } else {
+    if constexpr (K::S == 1) return 0u;  // lanes already differ in c
+    constexpr int KS0 = K::LOG2RX + 4 * (K::S - 2);
+    const int minb = 5 - log2C;  // ko bits >= minb are constant in a line
+    const int ks = KS0 > minb ? KS0 : minb;
+    return (ko >> ks) & 7u;
+  }
 }
 
 // ------------------------------------------------------------------ loads
@@ -146,200 +187,145 @@ __device__ __forceinline__ void a_store8(uint8_t* A, uint32_t m0, uint32_t k, ui
 // and writes the stage-1 A operand(s).
 //   contiguous input: sub-transform g = c*RX + k0, stage-1 row g*16^{S-1} + n^(2)
 //   strided input:    sub-transform g = k0*C + c, stage-1 row n^(2)*G + g
-template <int RX, bool SPLIT>
-__device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, int64_t t0) {
-  const int L = 1 << (4 * p.S);     // sub-transform length
-  const int Lq = L >> 4;            // 16^{S-1}
-  const int C = p.C;
+template <class K>
+__device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, const uint32_t* gin,
+                                            int log2C, int nvalid) {
+  constexpr int RX = K::RX;
   uint8_t* Alo = A + p.tiles * kTileBytes;
-  const float inv = 1.0f / 2048.0f;
-  if (p.in_contig) {
-    const int blocks = L >> 3;  // 8-point blocks per sub-transform
-    const int items = C * blocks;
-    for (int it = threadIdx.x; it < items; it += kThreads) {
-      const int c = it / blocks;
-      const int nb = (it - c * blocks) << 3;
-      const int64_t t = t0 + c;
-      const bool valid = t < p.T;
-      const int64_t base = valid ? side_base(p.in_l, t, p.log2I1, p.log2I2) : 0;
-      uint32_t hv[RX][8], lv[RX][8];
+  const uint32_t* gin_lo = gin + p.in_plane;
+  const int C = 1 << log2C;
+  // items: 8 points (contiguous: of one transform; strided: of 8 transforms)
+  constexpr int BLOG = K::LOG2L - 3;
+  const int items = K::IN_C ? (C << BLOG) : (K::L << (log2C - 3));
+  for (int it = threadIdx.x; it < items; it += kThreads) {
+    int c, np;  // transform (first of 8 when strided), point n' in [0, L)
+    uint32_t off0, step;
+    bool valid = true;
+    if constexpr (K::IN_C) {
+      c = it >> BLOG;
+      np = (it & ((1 << BLOG) - 1)) << 3;
+      off0 = ((uint32_t)c << K::LOG2N) + np;
+      step = K::L;
+      valid = c < nvalid;
+    } else {
+      const int cbm = (1 << (log2C - 3)) - 1;
+      c = (it & cbm) << 3;
+      np = it >> (log2C - 3);
+      off0 = (uint32_t)c + (uint32_t)np * p.in_l.es;
+      step = (uint32_t)K::L * p.in_l.es;
+    }
+    uint32_t hv[RX][8], lv[RX][8];
 #pragma unroll
-      for (int n0 = 0; n0 < RX; ++n0) {
-        uint4 a = make_uint4(0, 0, 0, 0), b = a, c2 = a, d = a;
+    for (int n0 = 0; n0 < RX; ++n0) {
+      uint4 a = make_uint4(0, 0, 0, 0), b = a;
+      if (valid) {
+        const uint4* src = reinterpret_cast<const uint4*>(gin + off0 + n0 * step);
+        a = __ldg(src);
+        b = __ldg(src + 1);
+      }
+      hv[n0][0] = a.x; hv[n0][1] = a.y; hv[n0][2] = a.z; hv[n0][3] = a.w;
+      hv[n0][4] = b.x; hv[n0][5] = b.y; hv[n0][6] = b.z; hv[n0][7] = b.w;
+      if constexpr (K::SPLIT) {
+        uint4 c2 = make_uint4(0, 0, 0, 0), d = c2;
         if (valid) {
-          const uint4* src = reinterpret_cast<const uint4*>(p.in + base + n0 * L + nb);
-          a = __ldg(src);
-          b = __ldg(src + 1);
-          if constexpr (SPLIT) {
-            const uint4* s2 = reinterpret_cast<const uint4*>(p.in + p.in_plane + base + n0 * L + nb);
-            c2 = __ldg(s2);
-            d = __ldg(s2 + 1);
-          }
+          const uint4* s2 = reinterpret_cast<const uint4*>(gin_lo + off0 + n0 * step);
+          c2 = __ldg(s2);
+          d = __ldg(s2 + 1);
         }
-        hv[n0][0] = a.x; hv[n0][1] = a.y; hv[n0][2] = a.z; hv[n0][3] = a.w;
-        hv[n0][4] = b.x; hv[n0][5] = b.y; hv[n0][6] = b.z; hv[n0][7] = b.w;
         lv[n0][0] = c2.x; lv[n0][1] = c2.y; lv[n0][2] = c2.z; lv[n0][3] = c2.w;
         lv[n0][4] = d.x; lv[n0][5] = d.y; lv[n0][6] = d.z; lv[n0][7] = d.w;
       }
-      if constexpr (RX > 1) {
+    }
+    if constexpr (RX > 1) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          float2 v[RX];
+      for (int i = 0; i < 8; ++i) {
+        float2 v[RX];
 #pragma unroll
-          for (int n0 = 0; n0 < RX; ++n0) {
-            v[n0] = h2f(hv[n0][i]);
-            if constexpr (SPLIT) {
-              float2 l = h2f(lv[n0][i]);
-              v[n0].x = fmaf(l.x, inv, v[n0].x);
-              v[n0].y = fmaf(l.y, inv, v[n0].y);
-            }
-          }
-          small_dft<RX>(v);
-          const int np = nb + i;  // n' of this point
-#pragma unroll
-          for (int k0 = 0; k0 < RX; ++k0) {
-            float2 y = v[k0];
-            if (k0) y = cmulf(y, tw_lookup(p.tw_lo, p.tw_hi, (uint64_t)k0 * np, p.log2N, p.tw_log2S));
-            hv[k0][i] = f2h2(y.x, y.y);
-            if constexpr (SPLIT) {
-              float2 hf = h2f(hv[k0][i]);
-              lv[k0][i] = f2h2((y.x - hf.x) * 2048.0f, (y.y - hf.y) * 2048.0f);
-            }
+        for (int n0 = 0; n0 < RX; ++n0) {
+          v[n0] = h2f(hv[n0][i]);
+          if constexpr (K::SPLIT) {
+            const float2 l = h2f(lv[n0][i]);
+            v[n0].x = fmaf(l.x, 1.0f / 2048.0f, v[n0].x);
+            v[n0].y = fmaf(l.y, 1.0f / 2048.0f, v[n0].y);
           }
         }
+        small_dft<RX>(v);
+        const uint32_t npi = K::IN_C ? (uint32_t)(np + i) : (uint32_t)np;
+#pragma unroll
+        for (int k0 = 0; k0 < RX; ++k0) {
+          float2 y = v[k0];
+          if (k0) y = cmulf(y, tw_lookup(p.tw_lo, p.tw_hi, (uint32_t)k0 * npi, K::LOG2N, p.tw_log2S));
+          hv[k0][i] = f2h2(y.x, y.y);
+          if constexpr (K::SPLIT) lv[k0][i] = split_lo(y.x, y.y, hv[k0][i]);
+        }
       }
-      const int n1 = nb / Lq;  // valid when Lq >= 8
+    }
+    if constexpr (K::IN_C) {
 #pragma unroll
       for (int k0 = 0; k0 < RX; ++k0) {
-        const int g = c * RX + k0;
-        if (Lq >= 8) {
-          const uint32_t m0 = (uint32_t)g * Lq + (nb & (Lq - 1));
-          uint4 re = make_uint4(__byte_perm(hv[k0][0], hv[k0][1], 0x5410), __byte_perm(hv[k0][2], hv[k0][3], 0x5410),
-                                __byte_perm(hv[k0][4], hv[k0][5], 0x5410), __byte_perm(hv[k0][6], hv[k0][7], 0x5410));
-          uint4 im = make_uint4(__byte_perm(hv[k0][0], hv[k0][1], 0x7632), __byte_perm(hv[k0][2], hv[k0][3], 0x7632),
-                                __byte_perm(hv[k0][4], hv[k0][5], 0x7632), __byte_perm(hv[k0][6], hv[k0][7], 0x7632));
-          a_store8(A, m0, n1, re, im);
-          if constexpr (SPLIT) {
-            uint4 re2 = make_uint4(__byte_perm(lv[k0][0], lv[k0][1], 0x5410), __byte_perm(lv[k0][2], lv[k0][3], 0x5410),
-                                   __byte_perm(lv[k0][4], lv[k0][5], 0x5410), __byte_perm(lv[k0][6], lv[k0][7], 0x5410));
-            uint4 im2 = make_uint4(__byte_perm(lv[k0][0], lv[k0][1], 0x7632), __byte_perm(lv[k0][2], lv[k0][3], 0x7632),
-                                   __byte_perm(lv[k0][4], lv[k0][5], 0x7632), __byte_perm(lv[k0][6], lv[k0][7], 0x7632));
-            a_store8(Alo, m0, n1, re2, im2);
-          }
+        const uint32_t g = ((uint32_t)c << K::LOG2RX) + k0;
+        if constexpr (K::LQ >= 8) {
+          const uint32_t m0 = (g << K::LOG2LQ) + (np & (K::LQ - 1));
+          const uint32_t n1 = (uint32_t)np >> K::LOG2LQ;
+          a_store8c(A, m0, n1, hv[k0]);
+          if constexpr (K::SPLIT) a_store8c(Alo, m0, n1, lv[k0]);
         } else {
           // S == 1: the 8 points are 8 different inputs of butterfly row g
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            const uint32_t k = (uint32_t)(nb + i);
+            const uint32_t k = (uint32_t)(np + i);
             *reinterpret_cast<uint16_t*>(A + a_off(g, k)) = (uint16_t)(hv[k0][i] & 0xFFFFu);
             *reinterpret_cast<uint16_t*>(A + a_off(g, 16 + k)) = (uint16_t)(hv[k0][i] >> 16);
-            if constexpr (SPLIT) {
+            if constexpr (K::SPLIT) {
               *reinterpret_cast<uint16_t*>(Alo + a_off(g, k)) = (uint16_t)(lv[k0][i] & 0xFFFFu);
               *reinterpret_cast<uint16_t*>(Alo + a_off(g, 16 + k)) = (uint16_t)(lv[k0][i] >> 16);
             }
           }
         }
       }
-    }
-  } else {
-    // strided input: 8 adjacent transforms per 32-byte read
-    const int cb_n = C >> 3;
-    const int items = cb_n * L;
-    const int G = C * RX;
-    const int64_t base0 = side_base(p.in_l, t0, p.log2I1, p.log2I2);
-    for (int it = threadIdx.x; it < items; it += kThreads) {
-      const int cb = it % cb_n;
-      const int np = it / cb_n;  // n' in [0, L)
-      const int c0 = cb << 3;
-      uint32_t hv[RX][8], lv[RX][8];
-#pragma unroll
-      for (int n0 = 0; n0 < RX; ++n0) {
-        const int64_t off = base0 + c0 + (int64_t)(n0 * L + np) * p.in_l.es;
-        const uint4* src = reinterpret_cast<const uint4*>(p.in + off);
-        uint4 a = __ldg(src), b = __ldg(src + 1);
-        hv[n0][0] = a.x; hv[n0][1] = a.y; hv[n0][2] = a.z; hv[n0][3] = a.w;
-        hv[n0][4] = b.x; hv[n0][5] = b.y; hv[n0][6] = b.z; hv[n0][7] = b.w;
-        if constexpr (SPLIT) {
-          const uint4* s2 = reinterpret_cast<const uint4*>(p.in + p.in_plane + off);
-          uint4 c2 = __ldg(s2), d = __ldg(s2 + 1);
-          lv[n0][0] = c2.x; lv[n0][1] = c2.y; lv[n0][2] = c2.z; lv[n0][3] = c2.w;
-          lv[n0][4] = d.x; lv[n0][5] = d.y; lv[n0][6] = d.z; lv[n0][7] = d.w;
-        }
-      }
-      if constexpr (RX > 1) {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          float2 v[RX];
-#pragma unroll
-          for (int n0 = 0; n0 < RX; ++n0) {
-            v[n0] = h2f(hv[n0][i]);
-            if constexpr (SPLIT) {
-              float2 l = h2f(lv[n0][i]);
-              v[n0].x = fmaf(l.x, inv, v[n0].x);
-              v[n0].y = fmaf(l.y, inv, v[n0].y);
-            }
-          }
-          small_dft<RX>(v);
-#pragma unroll
-          for (int k0 = 0; k0 < RX; ++k0) {
-            float2 y = v[k0];
-            if (k0) y = cmulf(y, tw_lookup(p.tw_lo, p.tw_hi, (uint64_t)k0 * np, p.log2N, p.tw_log2S));
-            hv[k0][i] = f2h2(y.x, y.y);
-            if constexpr (SPLIT) {
-              float2 hf = h2f(hv[k0][i]);
-              lv[k0][i] = f2h2((y.x - hf.x) * 2048.0f, (y.y - hf.y) * 2048.0f);
-            }
-          }
-        }
-      }
-      const int n1 = np / Lq;
-      const int nrest = np & (Lq - 1);
+    } else {
+      const uint32_t n1 = (uint32_t)np >> K::LOG2LQ;
+      const uint32_t nrest = (uint32_t)np & (K::LQ - 1);
 #pragma unroll
       for (int k0 = 0; k0 < RX; ++k0) {
-        const uint32_t m0 = (uint32_t)nrest * G + k0 * C + c0;
-        uint4 re = make_uint4(__byte_perm(hv[k0][0], hv[k0][1], 0x5410), __byte_perm(hv[k0][2], hv[k0][3], 0x5410),
-                              __byte_perm(hv[k0][4], hv[k0][5], 0x5410), __byte_perm(hv[k0][6], hv[k0][7], 0x5410));
-        uint4 im = make_uint4(__byte_perm(hv[k0][0], hv[k0][1], 0x7632), __byte_perm(hv[k0][2], hv[k0][3], 0x7632),
-                              __byte_perm(hv[k0][4], hv[k0][5], 0x7632), __byte_perm(hv[k0][6], hv[k0][7], 0x7632));
-        a_store8(A, m0, n1, re, im);
-        if constexpr (SPLIT) {
-          uint4 re2 = make_uint4(__byte_perm(lv[k0][0], lv[k0][1], 0x5410), __byte_perm(lv[k0][2], lv[k0][3], 0x5410),
-                                 __byte_perm(lv[k0][4], lv[k0][5], 0x5410), __byte_perm(lv[k0][6], lv[k0][7], 0x5410));
-          uint4 im2 = make_uint4(__byte_perm(lv[k0][0], lv[k0][1], 0x7632), __byte_perm(lv[k0][2], lv[k0][3], 0x7632),
-                                 __byte_perm(lv[k0][4], lv[k0][5], 0x7632), __byte_perm(lv[k0][6], lv[k0][7], 0x7632));
-          a_store8(Alo, m0, n1, re2, im2);
-        }
+        const uint32_t m0 = (nrest << (log2C + K::LOG2RX)) + ((uint32_t)k0 << log2C) + c;
+        a_store8c(A, m0, n1, hv[k0]);
+        if constexpr (K::SPLIT) a_store8c(Alo, m0, n1, lv[k0]);
       }
     }
   }
 }
 
 // ---------------------------------------------------------------- kernel
-template <int RX, bool SPLIT>
-__global__ void __launch_bounds__(kThreads, SPLIT ? 2 : 4) pass_kernel(const PassParams p) {
+template <int LOG2N, int MODE, bool SPLIT>
+__global__ void __launch_bounds__(kThreads, SPLIT ? 2 : 4)
+    pass_kernel(const __grid_constant__ PassParams p) {
+  using K = PassCfg<LOG2N, MODE, SPLIT>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* A = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                           ~uintptr_t(1023));
   const int tiles = p.tiles;
-  const int planes = SPLIT ? 2 : 1;
-  uint8_t* Bs = A + planes * tiles * kTileBytes;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(Bs + planes * kBImageBytes);
+  uint8_t* Bs = A + K::PLANES * tiles * kTileBytes;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Bs + K::PLANES * kBImageBytes);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
-  int* sflag = reinterpret_cast<int*>(tslot + 1);
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const int64_t t0 = (int64_t)blockIdx.x * p.C;
+  const int log2C = p.log2C;
+  const int C = 1 << log2C;
+  const int64_t t0 = (int64_t)blockIdx.x << log2C;
+  const int nvalid = (p.T - t0) < C ? (int)(p.T - t0) : C;
+  const uint32_t* gin = p.in + side_base(p.in_l, t0, p.log2I1, p.log2I2);
+  uint32_t* gout = p.out + side_base(p.out_l, t0, p.log2I1, p.log2I2);
 
   // DFT matrix image(s) -> shared memory
   {
     const uint4* src = reinterpret_cast<const uint4*>(p.dft_b);
     uint4* dst = reinterpret_cast<uint4*>(Bs);
-    for (int i = tid; i < planes * kBImageBytes / 16; i += kThreads) dst[i] = __ldg(src + i);
+    for (int i = tid; i < K::PLANES * kBImageBytes / 16; i += kThreads) dst[i] = __ldg(src + i);
   }
   if (tid == 0) {
     mbar_init(smem_u32(mbar), 1);
-    *sflag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -347,15 +333,10 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 2 : 4) pass_kernel(const Pas
     tmem_relinquish();
   }
 
-  load_stage1<RX, SPLIT>(p, A, t0);
+  load_stage1<K>(p, A, gin, log2C, nvalid);
 
-  const int S = p.S;
-  constexpr int log2RX = (RX == 1) ? 0 : (RX == 2) ? 1 : (RX == 4) ? 2 : 3;
-  const int N = 1 << p.log2N;
-  const int C = p.C;
-  const int G = C * RX;
-  const uint32_t Lq = 1u << (4 * (S - 1));
-  const uint32_t rows_valid = ((uint32_t)C << p.log2N) >> 4;  // butterflies per stage
+  const uint32_t rows_valid = (uint32_t)C << (LOG2N - 4);  // butterflies per stage
+  const uint32_t log2G = (uint32_t)log2C + K::LOG2RX;      // sub-transforms per CTA
 
   fence_proxy_async_smem();
   tc_fence_before_sync();
@@ -366,7 +347,8 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 2 : 4) pass_kernel(const Pas
   const uint32_t a_base = smem_u32(A), b_base = smem_u32(Bs);
   bool ok = true;
 
-  for (int j = 1; j <= S; ++j) {
+#pragma unroll
+  for (int j = 1; j <= K::S; ++j) {
     if (tid == 0) {
       tc_fence_after_sync();
       for (int t = 0; t < tiles; ++t) {
@@ -397,7 +379,7 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 2 : 4) pass_kernel(const Pas
     }
     tc_fence_after_sync();
 
-    const bool last = (j == S);
+    const bool last = (j == K::S);
     for (int t = 0; t < tiles; ++t) {
       const uint32_t row = (uint32_t)t * 128u + 32u * warp + lane;
       float re[16], im[16];
@@ -419,116 +401,111 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 2 : 4) pass_kernel(const Pas
           }
         }
       }
-
       if (row >= rows_valid) continue;  // padding rows of a partial last tile
 
-      // butterfly identity of this row at stage j
+      // butterfly identity of this row at stage j: sub-transform g, the
+      // digits kk = (k_1 .. k_{j-1}) already produced, and nrest = n^(j+1)
       uint32_t g, nrest, kk;
       if (j == 1) {
         kk = 0;
-        if (p.in_contig) {
-          g = row >> (4 * (S - 1));
-          nrest = row & (Lq - 1);
+        if constexpr (K::IN_C) {
+          g = row >> K::LOG2LQ;
+          nrest = row & (K::LQ - 1);
         } else {
-          nrest = row / (uint32_t)G;
-          g = row - nrest * (uint32_t)G;
+          nrest = row >> log2G;
+          g = row & ((1u << log2G) - 1u);
         }
       } else {
-        const uint32_t kkmask = (1u << (4 * (j - 1))) - 1u;
-        kk = row & kkmask;
-        const uint32_t q = row >> (4 * (j - 1));
-        g = q >> (4 * (S - j));
-        nrest = q & ((1u << (4 * (S - j))) - 1u);
+        const int sj = 4 * (j - 1);
+        kk = row & ((1u << sj) - 1u);
+        const uint32_t q = row >> sj;
+        const int sr = 4 * (K::S - j);
+        g = q >> sr;
+        nrest = q & ((1u << sr) - 1u);
       }
 
       if (!last) {
         // twiddle W_{L_j}^{k nrest}, L_j = 16^{S-j+1}; table is W_N
-        const uint64_t e1 = (uint64_t)nrest << (log2RX + 4 * (j - 1));
-        const float2 w = tw_lookup(p.tw_lo, p.tw_hi, e1, p.log2N, p.tw_log2S);
+        const float2 w = tw_lookup(p.tw_lo, p.tw_hi, nrest << (K::LOG2RX + 4 * (j - 1)), LOG2N,
+                                   p.tw_log2S);
         float2 tw = w;
 #pragma unroll
         for (int k = 1; k < 16; ++k) {
           const float xr = re[k], xi = im[k];
           re[k] = fmaf(xr, tw.x, -xi * tw.y);
           im[k] = fmaf(xr, tw.y, xi * tw.x);
-          tw = cmulf(tw, w);
+          if (k < 15) tw = cmulf(tw, w);
         }
-        const int sh = 4 * (S - j - 1);
+        const int sh = 4 * (K::S - j - 1);
         const uint32_t nnext = nrest >> sh;
         const uint32_t nlow = nrest & ((1u << sh) - 1u);
         const uint32_t dr = ((((g << sh) + nlow) << (4 * j)) + (kk << 4));
-        if constexpr (!SPLIT) {
-          uint4 r0 = make_uint4(f2h2(re[0], re[1]), f2h2(re[2], re[3]), f2h2(re[4], re[5]), f2h2(re[6], re[7]));
-          uint4 r1 = make_uint4(f2h2(re[8], re[9]), f2h2(re[10], re[11]), f2h2(re[12], re[13]), f2h2(re[14], re[15]));
-          uint4 i0 = make_uint4(f2h2(im[0], im[1]), f2h2(im[2], im[3]), f2h2(im[4], im[5]), f2h2(im[6], im[7]));
-          uint4 i1 = make_uint4(f2h2(im[8], im[9]), f2h2(im[10], im[11]), f2h2(im[12], im[13]), f2h2(im[14], im[15]));
-          a_store8(A, dr, nnext, r0, i0);
-          a_store8(A, dr + 8, nnext, r1, i1);
-        } else {
-          uint32_t hr[8], hi_[8], lr[8], li[8];
+        uint32_t h0[8], h1[8];
 #pragma unroll
-          for (int q2 = 0; q2 < 8; ++q2) {
-            hr[q2] = f2h2(re[2 * q2], re[2 * q2 + 1]);
-            hi_[q2] = f2h2(im[2 * q2], im[2 * q2 + 1]);
-            float2 a = h2f(hr[q2]), b = h2f(hi_[q2]);
-            lr[q2] = f2h2((re[2 * q2] - a.x) * 2048.0f, (re[2 * q2 + 1] - a.y) * 2048.0f);
-            li[q2] = f2h2((im[2 * q2] - b.x) * 2048.0f, (im[2 * q2 + 1] - b.y) * 2048.0f);
+        for (int k = 0; k < 8; ++k) {
+          h0[k] = f2h2(re[k], im[k]);
+          h1[k] = f2h2(re[8 + k], im[8 + k]);
+        }
+        a_store8c(A, dr, nnext, h0);
+        a_store8c(A, dr + 8, nnext, h1);
+        if constexpr (SPLIT) {
+          uint32_t l0[8], l1[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            l0[k] = split_lo(re[k], im[k], h0[k]);
+            l1[k] = split_lo(re[8 + k], im[8 + k], h1[k]);
           }
           uint8_t* Alo = A + tiles * kTileBytes;
-          a_store8(A, dr, nnext, make_uint4(hr[0], hr[1], hr[2], hr[3]), make_uint4(hi_[0], hi_[1], hi_[2], hi_[3]));
-          a_store8(A, dr + 8, nnext, make_uint4(hr[4], hr[5], hr[6], hr[7]), make_uint4(hi_[4], hi_[5], hi_[6], hi_[7]));
-          a_store8(Alo, dr, nnext, make_uint4(lr[0], lr[1], lr[2], lr[3]), make_uint4(li[0], li[1], li[2], li[3]));
-          a_store8(Alo, dr + 8, nnext, make_uint4(lr[4], lr[5], lr[6], lr[7]), make_uint4(li[4], li[5], li[6], li[7]));
+          a_store8c(Alo, dr, nnext, l0);
+          a_store8c(Alo, dr + 8, nnext, l1);
         }
       } else {
         // final stage: natural-order outputs into the staging copy
         uint32_t rev = 0;
         {
           uint32_t x = kk;
-          for (int d = 0; d < S - 1; ++d) {
+#pragma unroll
+          for (int d = 0; d < K::S - 1; ++d) {
             rev = (rev << 4) | (x & 15u);
             x >>= 4;
           }
         }
         uint32_t c, k0;
-        if (p.in_contig) {
-          c = g >> log2RX;
-          k0 = g & (RX - 1);
+        if constexpr (K::IN_C) {
+          c = g >> K::LOG2RX;
+          k0 = g & (K::RX - 1);
         } else {
-          k0 = g / (uint32_t)C;
-          c = g - k0 * (uint32_t)C;
+          k0 = g >> log2C;
+          c = g & ((1u << log2C) - 1u);
         }
-        const uint32_t kbase = k0 + (rev << log2RX);       // output index for k_S = 0
-        const uint32_t kstep = Lq << log2RX;               // output index step per k_S
+        const uint32_t kbase = k0 + (rev << K::LOG2RX);           // output index at k_S = 0
+        constexpr uint32_t kstep = (uint32_t)K::LQ << K::LOG2RX;  // output index step per k_S
         if (p.otw_level) {
           const int64_t t = t0 + c;
-          const int64_t col = (p.otw_level == 1) ? (t & ((int64_t(1) << p.log2I1) - 1))
-                                                 : ((t >> p.log2I1) & ((int64_t(1) << p.log2I2) - 1));
-          const float2 w0 = tw_lookup(p.otw_lo, p.otw_hi, (uint64_t)col * kbase, p.otw_log2M, p.otw_log2S);
-          const float2 ws = tw_lookup(p.otw_lo, p.otw_hi, (uint64_t)col * kstep, p.otw_log2M, p.otw_log2S);
+          const uint32_t col = (p.otw_level == 1)
+                                   ? (uint32_t)(t & ((int64_t(1) << p.log2I1) - 1))
+                                   : (uint32_t)((t >> p.log2I1) & ((int64_t(1) << p.log2I2) - 1));
+          const float2 w0 = tw_lookup(p.otw_lo, p.otw_hi, col * kbase, p.otw_log2M, p.otw_log2S);
+          const float2 ws = tw_lookup(p.otw_lo, p.otw_hi, col * kstep, p.otw_log2M, p.otw_log2S);
           float2 tw = w0;
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
             const float xr = re[k], xi = im[k];
             re[k] = fmaf(xr, tw.x, -xi * tw.y);
             im[k] = fmaf(xr, tw.y, xi * tw.x);
-            tw = cmulf(tw, ws);
+            if (k < 15) tw = cmulf(tw, ws);
           }
         }
         uint32_t* stg = reinterpret_cast<uint32_t*>(A);
-        const uint32_t P = (uint32_t)C * (uint32_t)N;
+        const uint32_t P = (uint32_t)C << LOG2N;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
           const uint32_t ko = kbase + kstep * k;
-          const uint32_t idx = p.out_contig ? (c * (uint32_t)N + ko) : (ko * (uint32_t)C + c);
-          if constexpr (!SPLIT) {
-            stg[stg_word(idx)] = f2h2(re[k], im[k]);
-          } else {
-            const uint32_t h = f2h2(re[k], im[k]);
-            const float2 hf = h2f(h);
-            stg[stg_word(idx)] = h;
-            stg[P + stg_word(idx)] = f2h2((re[k] - hf.x) * 2048.0f, (im[k] - hf.y) * 2048.0f);
-          }
+          const uint32_t idx = (K::OUT_C ? ((c << LOG2N) + ko) : ((ko << log2C) + c)) ^
+                               (stg_key<K>(ko, log2C) << 2);
+          const uint32_t h = f2h2(re[k], im[k]);
+          stg[idx] = h;
+          if constexpr (SPLIT) stg[P + idx] = split_lo(re[k], im[k], h);
         }
       }
     }
@@ -540,31 +517,26 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 2 : 4) pass_kernel(const Pas
   if (ok) {
     // copy-out: staging (natural order, chunk-swizzled) -> global, 16-byte stores
     const uint4* stg = reinterpret_cast<const uint4*>(A);
-    const uint32_t P = (uint32_t)C * (uint32_t)N;
-    const uint32_t nchunks = P >> 2;
-    if (p.out_contig) {
-      const uint32_t cpt = (uint32_t)N >> 2;  // chunks per transform
-      for (uint32_t q = tid; q < nchunks; q += kThreads) {
-        const uint32_t c = q / cpt;
-        const uint32_t e0 = (q - c * cpt) << 2;
-        const int64_t t = t0 + c;
-        if (t < p.T) {
-          const int64_t off = side_base(p.out_l, t, p.log2I1, p.log2I2) + e0;
-          const uint32_t pq = q ^ ((q >> 3) & 7u);
-          *reinterpret_cast<uint4*>(p.out + off) = stg[pq];
-          if constexpr (SPLIT) *reinterpret_cast<uint4*>(p.out + p.out_plane + off) = stg[nchunks + pq];
-        }
+    const uint32_t nchunks = ((uint32_t)C << LOG2N) >> 2;
+    if constexpr (K::OUT_C) {
+      const uint32_t vchunks = ((uint32_t)nvalid << LOG2N) >> 2;
+      for (uint32_t q = tid; q < vchunks; q += kThreads) {
+        const uint32_t ko = (q << 2) & (K::N - 1);
+        const uint32_t pq = q ^ stg_key<K>(ko, log2C);
+        *reinterpret_cast<uint4*>(gout + (q << 2)) = stg[pq];
+        if constexpr (SPLIT)
+          *reinterpret_cast<uint4*>(gout + p.out_plane + (q << 2)) = stg[nchunks + pq];
       }
     } else {
-      const uint32_t cpr = (uint32_t)C >> 2;  // chunks per output element index
-      const int64_t base0 = side_base(p.out_l, t0, p.log2I1, p.log2I2);
+      const int cq = log2C - 2;  // log2 of the chunks per output element index
+      const uint32_t es = p.out_l.es;
       for (uint32_t q = tid; q < nchunks; q += kThreads) {
-        const uint32_t k = q / cpr;
-        const uint32_t cc = (q - k * cpr) << 2;
-        const int64_t off = base0 + cc + (int64_t)k * p.out_l.es;
-        const uint32_t pq = q ^ ((q >> 3) & 7u);
-        *reinterpret_cast<uint4*>(p.out + off) = stg[pq];
-        if constexpr (SPLIT) *reinterpret_cast<uint4*>(p.out + p.out_plane + off) = stg[nchunks + pq];
+        const uint32_t ko = q >> cq;
+        const uint32_t cc = (q & ((1u << cq) - 1u)) << 2;
+        const uint32_t off = ko * es + cc;
+        const uint32_t pq = q ^ stg_key<K>(ko, log2C);
+        *reinterpret_cast<uint4*>(gout + off) = stg[pq];
+        if constexpr (SPLIT) *reinterpret_cast<uint4*>(gout + p.out_plane + off) = stg[nchunks + pq];
       }
     }
   }

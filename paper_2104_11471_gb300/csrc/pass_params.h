@@ -10,11 +10,20 @@ namespace tcfft {
 //   t1 = t & (I1 - 1), t2 = (t >> log2I1) & (I2 - 1), t3 = t >> (log2I1 + log2I2)
 // and its first element sits at t1*s1 + t2*s2 + t3*s3 (complex elements).
 // Element e of the transform sits at first + e*es.  A side is "contiguous"
-// when es == 1; otherwise it is "strided", and the CTA's group of C
-// transforms must be C consecutive t1 values with s1 == 1, so that every
-// element index reads or writes one run of C adjacent complex values.
+// when es == 1 (then s1 == N: the C transforms of a CTA form one block of
+// C*N elements); otherwise it is "strided" (s1 == 1: element e of the CTA's
+// C transforms is one run of C adjacent complex values).  The C transforms
+// of a CTA never straddle a t1 run (C divides I1).
 struct SideLayout {
-  int64_t s1, s2, s3, es;
+  int64_t s1, s2, s3;
+  uint32_t es;
+};
+
+// Pass modes (input side / output side).
+enum PassMode : int {
+  kModeContig = 0,    // contiguous in, contiguous out
+  kModeStrided = 1,   // strided in, strided out
+  kModeToStrided = 2  // contiguous in, strided out
 };
 
 struct PassParams {
@@ -22,16 +31,13 @@ struct PassParams {
   uint32_t* out;
   int64_t in_plane;     // split precision: element offset of the lo plane
   int64_t out_plane;
-  int S;                // radix-16 stages (1..3)
-  int R;                // leading radix on CUDA cores (1, 2, 4, 8)
-  int log2N;            // N = R * 16^S
-  int C;                // transforms per CTA
-  int tiles;            // 128-butterfly MMA tiles per stage = C*N/2048
+  int log2N;            // transform length of the pass (must match the kernel)
+  int log2C;            // transforms per CTA
+  int tiles;            // 128-butterfly MMA tiles per stage = ceil(C*N/2048)
   int tmem_cols;        // TMEM columns allocated per CTA
   int64_t T;            // transforms in the pass
   int log2I1, log2I2;
   SideLayout in_l, out_l;
-  int in_contig, out_contig;
   // W_N table for this pass (factored: W_N^a = hi[a >> log2S] * lo[a & (S-1)])
   const float* tw_lo;   // float2 pairs
   const float* tw_hi;
@@ -55,5 +61,11 @@ constexpr long long kWaitLimitCycles = 2000000000LL;  // ~1 s at 2 GHz
 
 // Device status codes written by kernels (mirror tcfft_status values).
 constexpr int kDevErrTimeout = 5;
+
+// Supported pass lengths per mode and precision (log2 N).
+constexpr int kMinLog2Pass = 4;
+constexpr int max_log2_pass(int mode, bool split) {
+  return mode == kModeContig ? (split ? 13 : 14) : (split ? 11 : 12);
+}
 
 }  // namespace tcfft

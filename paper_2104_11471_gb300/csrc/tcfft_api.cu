@@ -28,8 +28,22 @@
 #include "pass_params.h"
 
 namespace tcfft {
-cudaError_t launch_pass(const PassParams& p, bool split, dim3 grid, size_t smem, cudaStream_t s);
-cudaError_t configure_pass_kernel(bool split, size_t smem);
+const void* pass_fn_m0_plain(int log2N);
+const void* pass_fn_m1_plain(int log2N);
+const void* pass_fn_m2_plain(int log2N);
+const void* pass_fn_m0_split(int log2N);
+const void* pass_fn_m1_split(int log2N);
+const void* pass_fn_m2_split(int log2N);
+
+// kernel entry point for one (length, mode, precision), or null
+static const void* pass_fn(int log2N, int mode, bool split) {
+  if (log2N < kMinLog2Pass || log2N > max_log2_pass(mode, split)) return nullptr;
+  switch (mode) {
+    case kModeContig: return split ? pass_fn_m0_split(log2N) : pass_fn_m0_plain(log2N);
+    case kModeStrided: return split ? pass_fn_m1_split(log2N) : pass_fn_m1_plain(log2N);
+    default: return split ? pass_fn_m2_split(log2N) : pass_fn_m2_plain(log2N);
+  }
+}
 }  // namespace tcfft
 
 using namespace tcfft;
@@ -57,6 +71,7 @@ struct TwTable {
 
 struct Pass {
   PassParams p;
+  const void* fn;  // kernel entry point
   Buf src, dst;
   dim3 grid;
   size_t smem;
@@ -186,17 +201,25 @@ tcfft_status add_pass(tcfft_plan_s* pl, int64_t L, int64_t T, int64_t I1, int64_
   std::memset(&ps.p, 0, sizeof(ps.p));
   PassParams& p = ps.p;
   const int log2L = ilog2(L);
-  p.S = log2L / 4;
-  p.R = 1 << (log2L % 4);
   p.log2N = log2L;
-  if (p.S < 1) return TCFFT_ERR_INVALID_SIZE;
   const bool in_contig = in.es == 1, out_contig = out.es == 1;
+  int mode;
+  if (in_contig && out_contig) mode = kModeContig;
+  else if (!in_contig && !out_contig) mode = kModeStrided;
+  else if (in_contig) mode = kModeToStrided;
+  else return TCFFT_ERR_INVALID_SIZE;
+  // layout contract of the kernel (see SideLayout)
+  if ((in_contig && in.s1 != L) || (!in_contig && in.s1 != 1)) return TCFFT_ERR_INVALID_SIZE;
+  if ((out_contig && out.s1 != L) || (!out_contig && out.s1 != 1)) return TCFFT_ERR_INVALID_SIZE;
+  if (in.es * L >= (int64_t(1) << 31) || out.es * L >= (int64_t(1) << 31)) return TCFFT_ERR_INVALID_SIZE;
+  ps.fn = pass_fn(log2L, mode, pl->split);
+  if (!ps.fn) return TCFFT_ERR_INVALID_SIZE;
   const int64_t cap = pl->split ? kCapSplit : kCapPlain;
   int64_t C;
-  if (in_contig && out_contig) {
+  if (mode == kModeContig) {
     const int64_t target = pl->split ? 4096 : 8192;
     C = std::max<int64_t>(1, target / L);
-    if (C * L > cap) return TCFFT_ERR_INVALID_SIZE;
+    while (C > 1 && I1 % C != 0) C /= 2;
   } else {
     // strided side: C adjacent transforms per element index, C | I1, C >= 8
     const int64_t soft = pl->split ? 8192 : 16384;
@@ -211,10 +234,10 @@ tcfft_status add_pass(tcfft_plan_s* pl, int64_t L, int64_t T, int64_t I1, int64_
     if (C == 0) return TCFFT_ERR_INVALID_SIZE;
     // bring small transforms up to at least one full MMA tile when possible
     while (C * L < 2048 && I1 % (2 * C) == 0 && 2 * C * L <= cap) C *= 2;
-    if ((in.s1 != 1 && !in_contig) || (out.s1 != 1 && !out_contig)) return TCFFT_ERR_INVALID_SIZE;
   }
+  if (C * L > cap) return TCFFT_ERR_INVALID_SIZE;
   const int64_t P = C * L;
-  p.C = (int)C;
+  p.log2C = ilog2(C);
   p.tiles = (int)((P + 2047) / 2048);
   const int planes = pl->split ? 2 : 1;
   int cols = 32;
@@ -224,10 +247,8 @@ tcfft_status add_pass(tcfft_plan_s* pl, int64_t L, int64_t T, int64_t I1, int64_
   p.T = T;
   p.log2I1 = ilog2(I1);
   p.log2I2 = ilog2(I2);
-  p.in_l = SideLayout{in.s1, in.s2, in.s3, in.es};
-  p.out_l = SideLayout{out.s1, out.s2, out.s3, out.es};
-  p.in_contig = in_contig;
-  p.out_contig = out_contig;
+  p.in_l = SideLayout{in.s1, in.s2, in.s3, (uint32_t)in.es};
+  p.out_l = SideLayout{out.s1, out.s2, out.s3, (uint32_t)out.es};
   TwTable* tw = nullptr;
   tcfft_status st = pl->table(log2L, &tw);
   if (st != TCFFT_OK) return st;
@@ -260,6 +281,8 @@ tcfft_status add_pass(tcfft_plan_s* pl, int64_t L, int64_t T, int64_t I1, int64_
   if (smem < per_cta_max) smem = std::min<size_t>(per_cta_max, 227 * 1024);
   if (smem > 227 * 1024) return TCFFT_ERR_INVALID_SIZE;
   ps.smem = smem;
+  if (cudaFuncSetAttribute(ps.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return TCFFT_ERR_CUDA;
   pl->passes.push_back(ps);
   return TCFFT_OK;
 }
@@ -329,7 +352,6 @@ tcfft_status check_device() {
 }
 
 tcfft_status common_init(tcfft_plan_s* pl) {
-  if (configure_pass_kernel(pl->split, 227 * 1024) != cudaSuccess) return TCFFT_ERR_CUDA;
   if (cudaMalloc(&pl->d_status, sizeof(int)) != cudaSuccess) return TCFFT_ERR_ALLOC;
   if (cudaMemset(pl->d_status, 0, sizeof(int)) != cudaSuccess) return TCFFT_ERR_CUDA;
   if (cudaMalloc(&pl->dft_b, 2 * kBImageBytes) != cudaSuccess) return TCFFT_ERR_ALLOC;
@@ -422,7 +444,8 @@ tcfft_status tcfft_exec(tcfft_plan plan, const void* in, void* out, void* stream
     void* bufs[3] = {const_cast<void*>(in), out, plan->ws};
     p.in = reinterpret_cast<const uint32_t*>(bufs[ps.src]);
     p.out = reinterpret_cast<uint32_t*>(bufs[ps.dst]);
-    cudaError_t e = launch_pass(p, plan->split, ps.grid, ps.smem, s);
+    void* args[1] = {&p};
+    cudaError_t e = cudaLaunchKernel(ps.fn, ps.grid, dim3(kThreads), args, ps.smem, s);
     if (e != cudaSuccess) return TCFFT_ERR_LAUNCH;
   }
   return TCFFT_OK;
