@@ -262,6 +262,8 @@ def run_gpu(args, world, rank, local):
         tot_bytes += alg
         tot_ms += avg
         per_n.append({"n": n, "batch": b, "launches": p.num_launches, "ms": round(avg, 4),
+                      "passes": [{k: d[k] for k in ("log2n", "mode", "per_cta", "grid", "async_load", "smem", "ctas_per_sm", "regs")}
+                                 for d in p.describe()],
                       "gflops": round(flops_1d(n, b) / (avg / 1e3) / 1e9, 1),
                       "alg_gbs": round(alg / (avg / 1e3) / 1e9, 1),
                       "frac": round(alg / (avg / 1e3) / 1e9 / peak, 4)})

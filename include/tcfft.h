@@ -106,6 +106,12 @@ size_t tcfft_workspace_bytes(tcfft_plan plan);
 /* Number of kernel launches one tcfft_exec issues. */
 int tcfft_plan_num_launches(tcfft_plan plan);
 
+/* Writes a JSON description of the plan's kernel launches (length, layout
+ * mode, transforms per CTA, tiles, TMEM columns, shared memory, grid) into
+ * buf (at most len bytes, NUL-terminated).  Returns the length the full
+ * description needs, including the NUL; 0 for a NULL plan. */
+size_t tcfft_plan_describe(tcfft_plan plan, char* buf, size_t len);
+
 /* Human-readable name of a status code (static string). */
 const char* tcfft_status_string(tcfft_status status);
 

@@ -44,6 +44,7 @@ _SIG = {
     "tcfft_workspace_bytes": (ctypes.c_size_t, [_P]),
     "tcfft_plan_num_launches": (ctypes.c_int, [_P]),
     "tcfft_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "tcfft_plan_describe": (ctypes.c_size_t, [_P, ctypes.c_char_p, ctypes.c_size_t]),
 }
 
 _lock = threading.Lock()
@@ -128,6 +129,14 @@ def tcfft_plan_num_launches(plan: int) -> int:
     return lib().tcfft_plan_num_launches(plan)
 
 
+def tcfft_plan_describe(plan: int) -> list:
+    import json
+    n = lib().tcfft_plan_describe(plan, None, 0)
+    buf = ctypes.create_string_buffer(n)
+    lib().tcfft_plan_describe(plan, buf, n)
+    return json.loads(buf.value.decode())
+
+
 def tcfft_status_string(status: int) -> str:
     return lib().tcfft_status_string(status).decode()
 
@@ -177,6 +186,9 @@ class Plan:
     @property
     def num_launches(self) -> int:
         return tcfft_plan_num_launches(self.handle)
+
+    def describe(self) -> list:
+        return tcfft_plan_describe(self.handle)
 
     def exec(self, inp, out, stream=None) -> None:
         for t in (inp, out):

@@ -63,6 +63,9 @@ struct PassCfg {
   static constexpr bool OUT_C = MODE == kModeContig;
   static constexpr bool SPLIT = SPLIT_;
   static constexpr int PLANES = SPLIT ? 2 : 1;
+  // final outputs go straight to global memory when the lanes of a warp hold
+  // consecutive output indices (one or two radix-16 stages, contiguous out)
+  static constexpr bool DIRECT_OUT = OUT_C && S == 2;
   static_assert(S >= 1 && S <= 3, "pass length out of range");
 };
 
@@ -161,38 +164,94 @@ __device__ __forceinline__ void a_store8c(uint8_t* A, uint32_t m0, uint32_t k,
   *reinterpret_cast<uint4*>(A + a_off(m0, 16 + k)) = im;
 }
 
-// Staging-buffer swizzle for the final stage: the 16-byte chunk index inside
-// each 128-byte line is XORed with a key taken from output-index bits that
-// differ between the lanes of a warp and are constant inside the line, so
-// the single-word writes of one warp spread over the banks while the
-// copy-out still reads whole 16-byte chunks.
+// Staging-buffer swizzle for the final stage.  Output word (c, ko) of the
+// chunk lives at logical index c*N + ko (contiguous output) or ko*C + c
+// (strided output); its 16-byte chunk index inside each 128-byte line is
+// XORed with a key.  The key depends only on c and on ko bits below the
+// k_S digit (so one thread's 16 words share it), is constant inside a line
+// (so the XOR permutes whole chunks within their line), and is taken from
+// the digit that differs between the lanes of a warp, so the single-word
+// writes of one warp spread over the shared-memory banks.
 template <class K>
-__device__ __forceinline__ uint32_t stg_key(uint32_t ko, int log2C) {
+__device__ __forceinline__ uint32_t stg_key(uint32_t c, uint32_t ko, int log2C) {
+  constexpr int KSLO = K::LOG2RX + 4 * (K::S - 1);  // lowest bit of the k_S digit in ko
+  ko &= (1u << KSLO) - 1u;
   if constexpr (K::OUT_C) {
-    constexpr int KS0 = (K::S >= 2) ? (K::LOG2RX + 4 * (K::S - 2)) : 0;
-    constexpr int KS = KS0 > 5 ? KS0 : 5;  // ko bits >= 5 are constant in a line
-    if constexpr (K::N >= 32) return (ko >> KS) & 7u;
-    return 0u;
+    constexpr int LANE = (K::S >= 2) ? (K::LOG2RX + 4 * (K::S - 2)) : 0;
+    constexpr int KS = LANE > 5 ? LANE : 5;
+    constexpr int W = (KSLO - KS) < 3 ? (KSLO - KS) : 3;
+    if constexpr (K::S >= 2 && W > 0) {
+      return (ko >> KS) & ((1u << W) - 1u);
+    } else {
+      constexpr int CS = K::LOG2N >= 5 ? 0 : 5 - K::LOG2N;
+      return (c >> CS) & 7u;
+    }
   } else {
-    if constexpr (K::S == 1) return 0u;  // lanes already differ in c
-    constexpr int KS0 = K::LOG2RX + 4 * (K::S - 2);
-    const int minb = 5 - log2C;  // ko bits >= minb are constant in a line
-    const int ks = KS0 > minb ? KS0 : minb;
-    return (ko >> ks) & 7u;
+    if constexpr (K::S == 1) {
+      return 0u;
+    } else {
+      constexpr int LANE = K::LOG2RX + 4 * (K::S - 2);
+      const int line_min = log2C >= 5 ? 0 : 5 - log2C;
+      const int ks = LANE > line_min ? LANE : line_min;
+      const int w = (KSLO - ks) < 3 ? (KSLO - ks) : 3;
+      return w > 0 ? ((ko >> ks) & ((1u << w) - 1u)) : 0u;
+    }
   }
 }
 
 // ------------------------------------------------------------------ loads
+__device__ __forceinline__ void cp_async16(uint32_t dst_smem, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst_smem), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Issues the asynchronous copy of one chunk (C transforms) into the raw
+// buffer, keeping the global element order: contiguous input -> raw[c*N + e]
+// (one bulk copy per plane, completion on `lbar`), strided input ->
+// raw[e*C + c] (16-byte cp.async per thread).  Transforms past the end of
+// the batch are not copied: their rows only feed outputs that are dropped.
+template <class K>
+__device__ __forceinline__ void issue_raw_copy(const PassParams& p, uint32_t raw_s, uint32_t lbar,
+                                               const uint32_t* gin, int log2C, int nvalid) {
+  const uint32_t P = (uint32_t)1 << (log2C + K::LOG2N);
+  if constexpr (K::IN_C) {
+    if (threadIdx.x == 0) {
+      const uint32_t bytes = ((uint32_t)nvalid << K::LOG2N) * 4u;
+      mbar_arrive_expect_tx(lbar, bytes * K::PLANES);
+      bulk_g2s(raw_s, gin, bytes, lbar);
+      if constexpr (K::SPLIT) bulk_g2s(raw_s + P * 4u, gin + p.in_plane, bytes, lbar);
+    }
+  } else {
+    const uint32_t nq = P >> 2;  // 16-byte chunks per plane
+    const int cq = log2C - 2;
+#pragma unroll 1
+    for (int pl = 0; pl < K::PLANES; ++pl) {
+      const uint32_t* g = gin + (pl ? p.in_plane : 0);
+      const uint32_t dst0 = raw_s + pl * (P * 4u);
+      for (uint32_t q = threadIdx.x; q < nq; q += kThreads) {
+        const uint32_t off = (q >> cq) * p.in_l.es + ((q & ((1u << cq) - 1u)) << 2);
+        cp_async16(dst0 + (q << 4), g + off, 16);
+      }
+    }
+    cp_async_commit();
+  }
+}
+
 // Reads the CTA's C transforms, applies the leading radix-RX step (if any)
 // and writes the stage-1 A operand(s).
 //   contiguous input: sub-transform g = c*RX + k0, stage-1 row g*16^{S-1} + n^(2)
 //   strided input:    sub-transform g = k0*C + c, stage-1 row n^(2)*G + g
-template <class K>
-__device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, const uint32_t* gin,
-                                            int log2C, int nvalid) {
+// Source: global memory (SMEM = false; element e of transform c at
+// c*N + e or c + e*es) or the raw shared buffer (SMEM = true; es = C).
+template <class K, bool SMEM>
+__device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, const uint32_t* src,
+                                            const uint32_t* src_lo, uint32_t es, int log2C,
+                                            int nvalid) {
   constexpr int RX = K::RX;
   uint8_t* Alo = A + p.tiles * kTileBytes;
-  const uint32_t* gin_lo = gin + p.in_plane;
   const int C = 1 << log2C;
   // items: 8 points (contiguous: of one transform; strided: of 8 transforms)
   constexpr int BLOG = K::LOG2L - 3;
@@ -206,31 +265,37 @@ __device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, con
       np = (it & ((1 << BLOG) - 1)) << 3;
       off0 = ((uint32_t)c << K::LOG2N) + np;
       step = K::L;
-      valid = c < nvalid;
+      if constexpr (!SMEM) valid = c < nvalid;
     } else {
       const int cbm = (1 << (log2C - 3)) - 1;
       c = (it & cbm) << 3;
       np = it >> (log2C - 3);
-      off0 = (uint32_t)c + (uint32_t)np * p.in_l.es;
-      step = (uint32_t)K::L * p.in_l.es;
+      off0 = (uint32_t)c + (uint32_t)np * es;
+      step = (uint32_t)K::L * es;
     }
     uint32_t hv[RX][8], lv[RX][8];
 #pragma unroll
     for (int n0 = 0; n0 < RX; ++n0) {
       uint4 a = make_uint4(0, 0, 0, 0), b = a;
-      if (valid) {
-        const uint4* src = reinterpret_cast<const uint4*>(gin + off0 + n0 * step);
-        a = __ldg(src);
-        b = __ldg(src + 1);
+      const uint4* s4 = reinterpret_cast<const uint4*>(src + off0 + n0 * step);
+      if constexpr (SMEM) {
+        a = s4[0];
+        b = s4[1];
+      } else if (valid) {
+        a = __ldg(s4);
+        b = __ldg(s4 + 1);
       }
       hv[n0][0] = a.x; hv[n0][1] = a.y; hv[n0][2] = a.z; hv[n0][3] = a.w;
       hv[n0][4] = b.x; hv[n0][5] = b.y; hv[n0][6] = b.z; hv[n0][7] = b.w;
       if constexpr (K::SPLIT) {
         uint4 c2 = make_uint4(0, 0, 0, 0), d = c2;
-        if (valid) {
-          const uint4* s2 = reinterpret_cast<const uint4*>(gin_lo + off0 + n0 * step);
-          c2 = __ldg(s2);
-          d = __ldg(s2 + 1);
+        const uint4* l4 = reinterpret_cast<const uint4*>(src_lo + off0 + n0 * step);
+        if constexpr (SMEM) {
+          c2 = l4[0];
+          d = l4[1];
+        } else if (valid) {
+          c2 = __ldg(l4);
+          d = __ldg(l4 + 1);
         }
         lv[n0][0] = c2.x; lv[n0][1] = c2.y; lv[n0][2] = c2.z; lv[n0][3] = c2.w;
         lv[n0][4] = d.x; lv[n0][5] = d.y; lv[n0][6] = d.z; lv[n0][7] = d.w;
@@ -296,27 +361,55 @@ __device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, con
   }
 }
 
+// ---------------------------------------------------------------- epilogue
+// Packed FP32x2 complex multiply of two adjacent outputs by their twiddles:
+// (x + i y) (c + i d) = (x c - y d) + i (x d + y c), with nd = -d.
+__device__ __forceinline__ void cmul2(float2& x, float2& y, float2 c, float2 d, float2 nd) {
+  const float2 xr = __ffma2_rn(y, nd, __fmul2_rn(x, c));
+  const float2 xi = __ffma2_rn(y, c, __fmul2_rn(x, d));
+  x = xr;
+  y = xi;
+}
+
+// Byte offsets of the four 16-byte chunks a thread writes for one butterfly
+// (16 consecutive rows m0..m0+15 at input k of the next stage): re/im halves
+// of rows m0..m0+7 and m0+8..m0+15.  m0 is a multiple of 16.
+struct RowChunks {
+  uint32_t re0, re1;  // im chunks are 2048 bytes further (K + 16)
+};
+__device__ __forceinline__ RowChunks row_chunks(uint32_t m0, uint32_t k) {
+  RowChunks r;
+  r.re0 = a_off(m0, k);
+  r.re1 = r.re0 + ((k & 1u) ? -16 : 16);  // chunk index (2u+1) ^ k = ((2u) ^ k) ^ 1
+  return r;
+}
+
 // ---------------------------------------------------------------- kernel
+// Persistent: CTA b processes chunks b, b + gridDim.x, ... (C transforms
+// each).  With async_load, the raw input of the next chunk is copied into
+// shared memory (bulk copy or cp.async) while the current chunk runs its
+// MMA stages, epilogues and stores.
 template <int LOG2N, int MODE, bool SPLIT>
-__global__ void __launch_bounds__(kThreads, SPLIT ? 2 : 4)
+__global__ void __launch_bounds__(kThreads, SPLIT ? 1 : 2)
     pass_kernel(const __grid_constant__ PassParams p) {
   using K = PassCfg<LOG2N, MODE, SPLIT>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* A = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                           ~uintptr_t(1023));
   const int tiles = p.tiles;
-  uint8_t* Bs = A + K::PLANES * tiles * kTileBytes;
+  const int log2C = p.log2C;
+  const int C = 1 << log2C;
+  const uint32_t P = (uint32_t)C << LOG2N;  // points per chunk and plane
+  uint8_t* RAW = A + K::PLANES * tiles * kTileBytes;
+  uint8_t* Bs = RAW + (p.async_load ? K::PLANES * P * 4u : 0u);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(Bs + K::PLANES * kBImageBytes);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  uint64_t* lbar = mbar + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const int log2C = p.log2C;
-  const int C = 1 << log2C;
-  const int64_t t0 = (int64_t)blockIdx.x << log2C;
-  const int nvalid = (p.T - t0) < C ? (int)(p.T - t0) : C;
-  const uint32_t* gin = p.in + side_base(p.in_l, t0, p.log2I1, p.log2I2);
-  uint32_t* gout = p.out + side_base(p.out_l, t0, p.log2I1, p.log2I2);
+  const int quarter = warp & 3;  // TMEM lane quarter of this warp
+  const int half = warp >> 2;    // which tiles this warp takes in the epilogue
 
   // DFT matrix image(s) -> shared memory
   {
@@ -326,6 +419,7 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 2 : 4)
   }
   if (tid == 0) {
     mbar_init(smem_u32(mbar), 1);
+    mbar_init(smem_u32(lbar), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -333,214 +427,331 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 2 : 4)
     tmem_relinquish();
   }
 
-  load_stage1<K>(p, A, gin, log2C, nvalid);
-
   const uint32_t rows_valid = (uint32_t)C << (LOG2N - 4);  // butterflies per stage
   const uint32_t log2G = (uint32_t)log2C + K::LOG2RX;      // sub-transforms per CTA
+  const uint32_t idesc = make_idesc_f16(128, 32, 1, 0);
+  const uint32_t a_base = smem_u32(A), b_base = smem_u32(Bs), raw_s = smem_u32(RAW);
+  const uint32_t mbar_s = smem_u32(mbar), lbar_s = smem_u32(lbar);
+  const uint32_t* raw32 = reinterpret_cast<const uint32_t*>(RAW);
+  uint32_t phase = 0, lphase = 0;
+  bool ok = true, pending = false;  // pending: a bulk copy into RAW is in flight
 
-  fence_proxy_async_smem();
+  auto chunk_in = [&](int64_t ch) {
+    return p.in + side_base(p.in_l, ch << log2C, p.log2I1, p.log2I2);
+  };
+  auto chunk_valid = [&](int64_t ch) {
+    const int64_t left = p.T - (ch << log2C);
+    return left < C ? (int)left : C;
+  };
+
   tc_fence_before_sync();
-  __syncthreads();
+  __syncthreads();  // barriers initialised, TMEM address published
   tc_fence_after_sync();
   const uint32_t tmem = *tslot;
-  const uint32_t idesc = make_idesc_f16(128, 32, 1, 0);
-  const uint32_t a_base = smem_u32(A), b_base = smem_u32(Bs);
-  bool ok = true;
 
-#pragma unroll
-  for (int j = 1; j <= K::S; ++j) {
-    if (tid == 0) {
-      tc_fence_after_sync();
-      for (int t = 0; t < tiles; ++t) {
-        const uint32_t a = a_base + t * kTileBytes;
-        const uint32_t d = tmem + 32u * t;
-        mma_f16(d, make_smem_desc(a, 4096, 1024, 2), make_smem_desc(b_base, 128, 512, 0), idesc, 0);
-        mma_f16(d, make_smem_desc(a + 2048, 4096, 1024, 2), make_smem_desc(b_base + 256, 128, 512, 0),
-                idesc, 1);
-        if constexpr (SPLIT) {
-          const uint32_t alo = a + tiles * kTileBytes;
-          const uint32_t blo = b_base + kBImageBytes;
-          const uint32_t d2 = tmem + 32u * (tiles + t);
-          mma_f16(d2, make_smem_desc(alo, 4096, 1024, 2), make_smem_desc(b_base, 128, 512, 0), idesc, 0);
-          mma_f16(d2, make_smem_desc(alo + 2048, 4096, 1024, 2),
-                  make_smem_desc(b_base + 256, 128, 512, 0), idesc, 1);
-          mma_f16(d2, make_smem_desc(a, 4096, 1024, 2), make_smem_desc(blo, 128, 512, 0), idesc, 1);
-          mma_f16(d2, make_smem_desc(a + 2048, 4096, 1024, 2), make_smem_desc(blo + 256, 128, 512, 0),
-                  idesc, 1);
-        }
-      }
-      mma_commit(smem_u32(mbar));
-    }
-    const bool got = mbar_wait_bounded(smem_u32(mbar), (uint32_t)((j - 1) & 1), kWaitLimitCycles);
-    if (__syncthreads_or(!got)) {
-      if (tid == 0) atomicExch(p.status, kDevErrTimeout);
-      ok = false;
-      break;
-    }
-    tc_fence_after_sync();
+  int64_t chunk = blockIdx.x;
+  if (p.async_load && chunk < p.nchunks) {
+    issue_raw_copy<K>(p, raw_s, lbar_s, chunk_in(chunk), log2C, chunk_valid(chunk));
+    pending = K::IN_C;
+  }
 
-    const bool last = (j == K::S);
-    for (int t = 0; t < tiles; ++t) {
-      const uint32_t row = (uint32_t)t * 128u + 32u * warp + lane;
-      float re[16], im[16];
-      {
-        const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + 32u * t;
-        float v[32];
-        tmem_ld32_wait(taddr, v);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          re[k] = v[k];
-          im[k] = v[16 + k];
-        }
-        if constexpr (SPLIT) {
-          tmem_ld32_wait(taddr + 32u * tiles, v);
-#pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            re[k] = fmaf(v[k], 1.0f / 2048.0f, re[k]);
-            im[k] = fmaf(v[16 + k], 1.0f / 2048.0f, im[k]);
-          }
-        }
-      }
-      if (row >= rows_valid) continue;  // padding rows of a partial last tile
+  for (; chunk < p.nchunks; chunk += gridDim.x) {
+    const int64_t t0 = chunk << log2C;
+    const int nvalid = chunk_valid(chunk);
+    uint32_t* gout = p.out + side_base(p.out_l, t0, p.log2I1, p.log2I2);
 
-      // butterfly identity of this row at stage j: sub-transform g, the
-      // digits kk = (k_1 .. k_{j-1}) already produced, and nrest = n^(j+1)
-      uint32_t g, nrest, kk;
-      if (j == 1) {
-        kk = 0;
-        if constexpr (K::IN_C) {
-          g = row >> K::LOG2LQ;
-          nrest = row & (K::LQ - 1);
-        } else {
-          nrest = row >> log2G;
-          g = row & ((1u << log2G) - 1u);
+    if (p.async_load) {
+      if constexpr (K::IN_C) {
+        const bool got = mbar_wait_bounded(lbar_s, lphase, kWaitLimitCycles);
+        if (got) {
+          lphase ^= 1u;
+          pending = false;
+        }
+        if (__syncthreads_or(!got)) {
+          if (tid == 0) atomicExch(p.status, kDevErrTimeout);
+          ok = false;
+          break;
         }
       } else {
-        const int sj = 4 * (j - 1);
-        kk = row & ((1u << sj) - 1u);
-        const uint32_t q = row >> sj;
-        const int sr = 4 * (K::S - j);
-        g = q >> sr;
-        nrest = q & ((1u << sr) - 1u);
+        cp_async_wait_all();
+        __syncthreads();
       }
-
-      if (!last) {
-        // twiddle W_{L_j}^{k nrest}, L_j = 16^{S-j+1}; table is W_N
-        const float2 w = tw_lookup(p.tw_lo, p.tw_hi, nrest << (K::LOG2RX + 4 * (j - 1)), LOG2N,
-                                   p.tw_log2S);
-        float2 tw = w;
-#pragma unroll
-        for (int k = 1; k < 16; ++k) {
-          const float xr = re[k], xi = im[k];
-          re[k] = fmaf(xr, tw.x, -xi * tw.y);
-          im[k] = fmaf(xr, tw.y, xi * tw.x);
-          if (k < 15) tw = cmulf(tw, w);
-        }
-        const int sh = 4 * (K::S - j - 1);
-        const uint32_t nnext = nrest >> sh;
-        const uint32_t nlow = nrest & ((1u << sh) - 1u);
-        const uint32_t dr = ((((g << sh) + nlow) << (4 * j)) + (kk << 4));
-        uint32_t h0[8], h1[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          h0[k] = f2h2(re[k], im[k]);
-          h1[k] = f2h2(re[8 + k], im[8 + k]);
-        }
-        a_store8c(A, dr, nnext, h0);
-        a_store8c(A, dr + 8, nnext, h1);
-        if constexpr (SPLIT) {
-          uint32_t l0[8], l1[8];
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            l0[k] = split_lo(re[k], im[k], h0[k]);
-            l1[k] = split_lo(re[8 + k], im[8 + k], h1[k]);
-          }
-          uint8_t* Alo = A + tiles * kTileBytes;
-          a_store8c(Alo, dr, nnext, l0);
-          a_store8c(Alo, dr + 8, nnext, l1);
-        }
-      } else {
-        // final stage: natural-order outputs into the staging copy
-        uint32_t rev = 0;
-        {
-          uint32_t x = kk;
-#pragma unroll
-          for (int d = 0; d < K::S - 1; ++d) {
-            rev = (rev << 4) | (x & 15u);
-            x >>= 4;
-          }
-        }
-        uint32_t c, k0;
-        if constexpr (K::IN_C) {
-          c = g >> K::LOG2RX;
-          k0 = g & (K::RX - 1);
-        } else {
-          k0 = g >> log2C;
-          c = g & ((1u << log2C) - 1u);
-        }
-        const uint32_t kbase = k0 + (rev << K::LOG2RX);           // output index at k_S = 0
-        constexpr uint32_t kstep = (uint32_t)K::LQ << K::LOG2RX;  // output index step per k_S
-        if (p.otw_level) {
-          const int64_t t = t0 + c;
-          const uint32_t col = (p.otw_level == 1)
-                                   ? (uint32_t)(t & ((int64_t(1) << p.log2I1) - 1))
-                                   : (uint32_t)((t >> p.log2I1) & ((int64_t(1) << p.log2I2) - 1));
-          const float2 w0 = tw_lookup(p.otw_lo, p.otw_hi, col * kbase, p.otw_log2M, p.otw_log2S);
-          const float2 ws = tw_lookup(p.otw_lo, p.otw_hi, col * kstep, p.otw_log2M, p.otw_log2S);
-          float2 tw = w0;
-#pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const float xr = re[k], xi = im[k];
-            re[k] = fmaf(xr, tw.x, -xi * tw.y);
-            im[k] = fmaf(xr, tw.y, xi * tw.x);
-            if (k < 15) tw = cmulf(tw, ws);
-          }
-        }
-        uint32_t* stg = reinterpret_cast<uint32_t*>(A);
-        const uint32_t P = (uint32_t)C << LOG2N;
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const uint32_t ko = kbase + kstep * k;
-          const uint32_t idx = (K::OUT_C ? ((c << LOG2N) + ko) : ((ko << log2C) + c)) ^
-                               (stg_key<K>(ko, log2C) << 2);
-          const uint32_t h = f2h2(re[k], im[k]);
-          stg[idx] = h;
-          if constexpr (SPLIT) stg[P + idx] = split_lo(re[k], im[k], h);
-        }
+      load_stage1<K, true>(p, A, raw32, raw32 + P, K::IN_C ? 1u : (uint32_t)C, log2C, nvalid);
+      __syncthreads();  // raw buffer consumed: prefetch the next chunk into it
+      const int64_t next = chunk + gridDim.x;
+      if (next < p.nchunks) {
+        issue_raw_copy<K>(p, raw_s, lbar_s, chunk_in(next), log2C, chunk_valid(next));
+        pending = K::IN_C;
       }
+    } else {
+      const uint32_t* gin = chunk_in(chunk);
+      load_stage1<K, false>(p, A, gin, gin + p.in_plane, p.in_l.es, log2C, nvalid);
     }
+
     fence_proxy_async_smem();
     tc_fence_before_sync();
     __syncthreads();
-  }
 
-  if (ok) {
-    // copy-out: staging (natural order, chunk-swizzled) -> global, 16-byte stores
-    const uint4* stg = reinterpret_cast<const uint4*>(A);
-    const uint32_t nchunks = ((uint32_t)C << LOG2N) >> 2;
-    if constexpr (K::OUT_C) {
-      const uint32_t vchunks = ((uint32_t)nvalid << LOG2N) >> 2;
-      for (uint32_t q = tid; q < vchunks; q += kThreads) {
-        const uint32_t ko = (q << 2) & (K::N - 1);
-        const uint32_t pq = q ^ stg_key<K>(ko, log2C);
-        *reinterpret_cast<uint4*>(gout + (q << 2)) = stg[pq];
-        if constexpr (SPLIT)
-          *reinterpret_cast<uint4*>(gout + p.out_plane + (q << 2)) = stg[nchunks + pq];
+#pragma unroll
+    for (int j = 1; j <= K::S; ++j) {
+      if (tid == 0) {
+        tc_fence_after_sync();
+        for (int t = 0; t < tiles; ++t) {
+          const uint32_t a = a_base + t * kTileBytes;
+          const uint32_t d = tmem + 32u * t;
+          mma_f16(d, make_smem_desc(a, 4096, 1024, 2), make_smem_desc(b_base, 128, 512, 0), idesc, 0);
+          mma_f16(d, make_smem_desc(a + 2048, 4096, 1024, 2),
+                  make_smem_desc(b_base + 256, 128, 512, 0), idesc, 1);
+          if constexpr (SPLIT) {
+            const uint32_t alo = a + tiles * kTileBytes;
+            const uint32_t blo = b_base + kBImageBytes;
+            const uint32_t d2 = tmem + 32u * (tiles + t);
+            mma_f16(d2, make_smem_desc(alo, 4096, 1024, 2), make_smem_desc(b_base, 128, 512, 0),
+                    idesc, 0);
+            mma_f16(d2, make_smem_desc(alo + 2048, 4096, 1024, 2),
+                    make_smem_desc(b_base + 256, 128, 512, 0), idesc, 1);
+            mma_f16(d2, make_smem_desc(a, 4096, 1024, 2), make_smem_desc(blo, 128, 512, 0), idesc, 1);
+            mma_f16(d2, make_smem_desc(a + 2048, 4096, 1024, 2),
+                    make_smem_desc(blo + 256, 128, 512, 0), idesc, 1);
+          }
+        }
+        mma_commit(mbar_s);
       }
-    } else {
-      const int cq = log2C - 2;  // log2 of the chunks per output element index
-      const uint32_t es = p.out_l.es;
-      for (uint32_t q = tid; q < nchunks; q += kThreads) {
-        const uint32_t ko = q >> cq;
-        const uint32_t cc = (q & ((1u << cq) - 1u)) << 2;
-        const uint32_t off = ko * es + cc;
-        const uint32_t pq = q ^ stg_key<K>(ko, log2C);
-        *reinterpret_cast<uint4*>(gout + off) = stg[pq];
-        if constexpr (SPLIT) *reinterpret_cast<uint4*>(gout + p.out_plane + off) = stg[nchunks + pq];
+      const bool got = mbar_wait_bounded(mbar_s, phase, kWaitLimitCycles);
+      phase ^= 1u;
+      if (__syncthreads_or(!got)) {
+        if (tid == 0) atomicExch(p.status, kDevErrTimeout);
+        ok = false;
+        break;
+      }
+      tc_fence_after_sync();
+
+      const bool last = (j == K::S);
+      for (int t = half; t < tiles; t += 2) {
+        const uint32_t row = (uint32_t)t * 128u + 32u * quarter + lane;
+        // X[i] = (Re out 2i, Re out 2i+1), Y[i] = (Im out 2i, Im out 2i+1)
+        float2 X[8], Y[8];
+        {
+          const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + 32u * t;
+          float v[32];
+          tmem_ld32_wait(taddr, v);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            X[i] = make_float2(v[2 * i], v[2 * i + 1]);
+            Y[i] = make_float2(v[16 + 2 * i], v[16 + 2 * i + 1]);
+          }
+          if constexpr (SPLIT) {
+            tmem_ld32_wait(taddr + 32u * tiles, v);
+            const float2 s = make_float2(1.0f / 2048.0f, 1.0f / 2048.0f);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              X[i] = __ffma2_rn(make_float2(v[2 * i], v[2 * i + 1]), s, X[i]);
+              Y[i] = __ffma2_rn(make_float2(v[16 + 2 * i], v[16 + 2 * i + 1]), s, Y[i]);
+            }
+          }
+        }
+        if (row >= rows_valid) continue;  // padding rows of a partial last tile
+
+        // butterfly identity of this row at stage j: sub-transform g, the
+        // digits kk = (k_1 .. k_{j-1}) already produced, and nrest = n^(j+1)
+        uint32_t g, nrest, kk;
+        if (j == 1) {
+          kk = 0;
+          if constexpr (K::IN_C) {
+            g = row >> K::LOG2LQ;
+            nrest = row & (K::LQ - 1);
+          } else {
+            nrest = row >> log2G;
+            g = row & ((1u << log2G) - 1u);
+          }
+        } else {
+          const int sj = 4 * (j - 1);
+          kk = row & ((1u << sj) - 1u);
+          const uint32_t q = row >> sj;
+          const int sr = 4 * (K::S - j);
+          g = q >> sr;
+          nrest = q & ((1u << sr) - 1u);
+        }
+
+        if (!last) {
+          // twiddle W_{L_j}^{k nrest} = w^k, w = W_{L_j}^{nrest}: (w, w^2) read
+          // from the stage table, the pairs (w^{2i}, w^{2i+1}) advanced by w^2
+          {
+            int toff = 0;
+#pragma unroll
+            for (int i = 1; i < j; ++i) toff += 1 << (4 * (K::S - i));
+            const float4 e = __ldg(p.stw + toff + (int)nrest);
+            float2 c2 = make_float2(1.0f, e.x), d2 = make_float2(0.0f, e.y);  // (w^0, w^1)
+            const float2 sc = make_float2(e.z, e.z), sd = make_float2(e.w, e.w);
+            const float2 snd = make_float2(-e.w, -e.w);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              if (i > 0) cmul2(X[i], Y[i], c2, d2, make_float2(-d2.x, -d2.y));
+              else {
+                // k = 0 is untouched; k = 1 by w
+                const float xr = X[0].y, xi = Y[0].y;
+                X[0].y = fmaf(xr, e.x, -xi * e.y);
+                Y[0].y = fmaf(xr, e.y, xi * e.x);
+              }
+              if (i < 7) {
+                float2 cn = c2, dn = d2;
+                cmul2(cn, dn, sc, sd, snd);
+                c2 = cn;
+                d2 = dn;
+              }
+            }
+          }
+          const int sh = 4 * (K::S - j - 1);
+          const uint32_t nnext = nrest >> sh;
+          const uint32_t nlow = nrest & ((1u << sh) - 1u);
+          const uint32_t dr = ((((g << sh) + nlow) << (4 * j)) + (kk << 4));
+          const RowChunks rc = row_chunks(dr, nnext);
+          uint32_t hr[8], hi[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            hr[i] = f2h2(X[i].x, X[i].y);
+            hi[i] = f2h2(Y[i].x, Y[i].y);
+          }
+          *reinterpret_cast<uint4*>(A + rc.re0) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+          *reinterpret_cast<uint4*>(A + rc.re0 + 2048) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<uint4*>(A + rc.re1) = make_uint4(hr[4], hr[5], hr[6], hr[7]);
+          *reinterpret_cast<uint4*>(A + rc.re1 + 2048) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+          if constexpr (SPLIT) {
+            uint32_t lr[8], li[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              lr[i] = split_lo(X[i].x, X[i].y, hr[i]);
+              li[i] = split_lo(Y[i].x, Y[i].y, hi[i]);
+            }
+            uint8_t* Alo = A + tiles * kTileBytes;
+            *reinterpret_cast<uint4*>(Alo + rc.re0) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
+            *reinterpret_cast<uint4*>(Alo + rc.re0 + 2048) = make_uint4(li[0], li[1], li[2], li[3]);
+            *reinterpret_cast<uint4*>(Alo + rc.re1) = make_uint4(lr[4], lr[5], lr[6], lr[7]);
+            *reinterpret_cast<uint4*>(Alo + rc.re1 + 2048) = make_uint4(li[4], li[5], li[6], li[7]);
+          }
+        } else {
+          // final stage: natural-order outputs into the staging copy
+          uint32_t rev = 0;
+          {
+            uint32_t x = kk;
+#pragma unroll
+            for (int d = 0; d < K::S - 1; ++d) {
+              rev = (rev << 4) | (x & 15u);
+              x >>= 4;
+            }
+          }
+          uint32_t c, k0;
+          if constexpr (K::IN_C) {
+            c = g >> K::LOG2RX;
+            k0 = g & (K::RX - 1);
+          } else {
+            k0 = g >> log2C;
+            c = g & ((1u << log2C) - 1u);
+          }
+          const uint32_t kbase = k0 + (rev << K::LOG2RX);           // output index at k_S = 0
+          constexpr uint32_t kstep = (uint32_t)K::LQ << K::LOG2RX;  // output index step per k_S
+          if (p.otw_level) {
+            // W_M^{col (kbase + kstep k)}: powers of ws = W_M^{col kstep} from
+            // w0 = W_M^{col kbase}, advanced two outputs at a time
+            const int64_t t = t0 + c;
+            const uint32_t col = (p.otw_level == 1)
+                                     ? (uint32_t)(t & ((int64_t(1) << p.log2I1) - 1))
+                                     : (uint32_t)((t >> p.log2I1) & ((int64_t(1) << p.log2I2) - 1));
+            const float2 w0 = tw_lookup(p.otw_lo, p.otw_hi, col * kbase, p.otw_log2M, p.otw_log2S);
+            const float2 ws = tw_lookup(p.otw_lo, p.otw_hi, col * kstep, p.otw_log2M, p.otw_log2S);
+            const float2 w1 = cmulf(w0, ws), ws2 = cmulf(ws, ws);
+            float2 c2 = make_float2(w0.x, w1.x), d2 = make_float2(w0.y, w1.y);
+            const float2 sc = make_float2(ws2.x, ws2.x), sd = make_float2(ws2.y, ws2.y);
+            const float2 snd = make_float2(-ws2.y, -ws2.y);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              cmul2(X[i], Y[i], c2, d2, make_float2(-d2.x, -d2.y));
+              if (i < 7) {
+                float2 cn = c2, dn = d2;
+                cmul2(cn, dn, sc, sd, snd);
+                c2 = cn;
+                d2 = dn;
+              }
+            }
+          }
+          if constexpr (K::DIRECT_OUT) {
+            // lanes hold consecutive output indices: store straight to global
+            if ((int)c < nvalid) {
+              uint32_t* o = gout + (c << LOG2N) + kbase;
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const uint32_t h0 = f2h2(X[i].x, Y[i].x), h1 = f2h2(X[i].y, Y[i].y);
+                o[(2 * i) * kstep] = h0;
+                o[(2 * i + 1) * kstep] = h1;
+                if constexpr (SPLIT) {
+                  o[p.out_plane + (2 * i) * kstep] = split_lo(X[i].x, Y[i].x, h0);
+                  o[p.out_plane + (2 * i + 1) * kstep] = split_lo(X[i].y, Y[i].y, h1);
+                }
+              }
+            }
+            continue;
+          }
+          uint32_t* stg = reinterpret_cast<uint32_t*>(A);
+          const uint32_t key = stg_key<K>(c, kbase, log2C) << 2;
+          const uint32_t base = K::OUT_C ? ((c << LOG2N) + kbase) : ((kbase << log2C) + c);
+          const uint32_t wstep = K::OUT_C ? kstep : (kstep << log2C);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const uint32_t i0 = (base + (2 * i) * wstep) ^ key;
+            const uint32_t i1 = (base + (2 * i + 1) * wstep) ^ key;
+            const uint32_t h0 = f2h2(X[i].x, Y[i].x), h1 = f2h2(X[i].y, Y[i].y);
+            stg[i0] = h0;
+            stg[i1] = h1;
+            if constexpr (SPLIT) {
+              stg[P + i0] = split_lo(X[i].x, Y[i].x, h0);
+              stg[P + i1] = split_lo(X[i].y, Y[i].y, h1);
+            }
+          }
+        }
+      }
+      fence_proxy_async_smem();
+      tc_fence_before_sync();
+      __syncthreads();
+    }
+    if (!ok) break;
+
+    // copy-out: staging (natural order, chunk-swizzled) -> global, 16-byte stores
+    if constexpr (!K::DIRECT_OUT) {
+      const uint4* stg = reinterpret_cast<const uint4*>(A);
+      const uint32_t nch = P >> 2;
+      if constexpr (K::OUT_C) {
+        const uint32_t vchunks = ((uint32_t)nvalid << LOG2N) >> 2;
+        for (uint32_t q = tid; q < vchunks; q += kThreads) {
+          const uint32_t c = (q << 2) >> LOG2N;
+          const uint32_t ko = (q << 2) & (K::N - 1);
+          const uint32_t pq = q ^ stg_key<K>(c, ko, log2C);
+          *reinterpret_cast<uint4*>(gout + (q << 2)) = stg[pq];
+          if constexpr (SPLIT) *reinterpret_cast<uint4*>(gout + p.out_plane + (q << 2)) = stg[nch + pq];
+        }
+      } else {
+        const int cq = log2C - 2;  // log2 of the chunks per output element index
+        const uint32_t es = p.out_l.es;
+        for (uint32_t q = tid; q < nch; q += kThreads) {
+          const uint32_t ko = q >> cq;
+          const uint32_t cc = (q & ((1u << cq) - 1u)) << 2;
+          const uint32_t off = ko * es + cc;
+          const uint32_t pq = q ^ stg_key<K>(cc, ko, log2C);
+          *reinterpret_cast<uint4*>(gout + off) = stg[pq];
+          if constexpr (SPLIT) *reinterpret_cast<uint4*>(gout + p.out_plane + off) = stg[nch + pq];
+        }
       }
     }
+    __syncthreads();  // staging (= A) is rewritten by the next chunk
   }
 
+  // unwind: no copy may still target this CTA's shared memory when it exits
+  if (p.async_load) {
+    if constexpr (K::IN_C) {
+      if (pending) (void)mbar_wait_bounded(lbar_s, lphase, kWaitLimitCycles);
+    } else {
+      cp_async_wait_all();
+    }
+  }
   tc_fence_before_sync();
   __syncthreads();
   if (warp == 0) {

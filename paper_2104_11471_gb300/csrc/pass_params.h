@@ -38,6 +38,10 @@ struct PassParams {
   int64_t T;            // transforms in the pass
   int log2I1, log2I2;
   SideLayout in_l, out_l;
+  // Per-stage twiddle bases for radix-16 stages 1..S-1: entry (j, nrest) is
+  // (w, w^2), w = W_{L_j}^{nrest}, L_j = 16^{S-j+1}; stage j starts at entry
+  // sum_{i<j} 16^{S-i}.
+  const float4* stw;
   // W_N table for this pass (factored: W_N^a = hi[a >> log2S] * lo[a & (S-1)])
   const float* tw_lo;   // float2 pairs
   const float* tw_hi;
@@ -49,6 +53,8 @@ struct PassParams {
   int otw_log2S;
   const float* otw_lo;
   const float* otw_hi;
+  int async_load;         // 1: prefetch the next chunk with cp.async into a raw buffer
+  int64_t nchunks;        // CTA work items: ceil(T / C); CTAs loop over them
   const uint16_t* dft_b;  // radix-16 DFT matrix image(s) in the MMA B layout
   int* status;            // device error word (0 = ok)
 };
@@ -56,7 +62,7 @@ struct PassParams {
 constexpr int kTileRows = 128;        // butterflies per MMA tile (M)
 constexpr int kTileBytes = 8192;      // one tile of A: 128 rows x 32 halves
 constexpr int kBImageBytes = 2048;    // 32 x 32 halves, K-major, no swizzle
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;        // 8 warps: two per TMEM lane quarter
 constexpr long long kWaitLimitCycles = 2000000000LL;  // ~1 s at 2 GHz
 
 // Device status codes written by kernels (mirror tcfft_status values).

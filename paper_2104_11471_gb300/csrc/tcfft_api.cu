@@ -19,9 +19,11 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "../../include/tcfft.h"
@@ -75,6 +77,8 @@ struct Pass {
   Buf src, dst;
   dim3 grid;
   size_t smem;
+  int occ = 0;   // CTAs per SM the grid was sized for
+  int regs = 0;  // registers per thread of the kernel
 };
 
 // ------------------------------------------------------------- device code
@@ -91,6 +95,27 @@ __global__ void twiddle_table_kernel(float2* lo, float2* hi, int log2M, int log2
     const float2 w = make_float2((float)c, (float)s);
     if (i < S) lo[i] = w; else hi[i - S] = w;
   }
+}
+
+// Per-stage twiddle bases of a pass with S radix-16 stages (L = 16^S): stage
+// j = 1..S-1 owns R_j = 16^{S-j} entries starting at sum_{i<j} R_i; entry
+// nrest holds (w, w^2) as one float4, w = W_{L_j}^{nrest}, L_j = 16^{S-j+1}
+// (FP64 sincospi, rounded once to FP32).  Lanes of a warp read consecutive
+// entries.
+__global__ void stage_twiddle_kernel(float4* out, int S, int rows) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= rows) return;
+  int j = 1, off = 0;
+  while (j < S - 1 && row >= off + (1 << (4 * (S - j)))) {
+    off += 1 << (4 * (S - j));
+    ++j;
+  }
+  const int nrest = row - off;
+  const double Lj = (double)(1 << (4 * (S - j + 1)));
+  double s1, c1, s2, c2;
+  sincospi(-2.0 * (double)nrest / Lj, &s1, &c1);
+  sincospi(-4.0 * (double)nrest / Lj, &s2, &c2);
+  out[row] = make_float4((float)c1, (float)s1, (float)c2, (float)s2);
 }
 
 // B operand of the radix-16 stage: the real 32 x 32 form of F_16,
@@ -123,6 +148,12 @@ int ilog2(int64_t v) {
 }
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
+// Integer from the environment (debugging and tuning overrides), or dflt.
+int env_int(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  return (v && *v) ? std::atoi(v) : dflt;
+}
+
 tcfft_status from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return TCFFT_OK;
   if (e == cudaErrorMemoryAllocation) return TCFFT_ERR_ALLOC;
@@ -151,6 +182,7 @@ struct tcfft_plan_s {
       cudaFree(kv.second.lo);
       cudaFree(kv.second.hi);
     }
+    for (auto& kv : stage_tables) cudaFree(kv.second);
     cudaFree(dft_b);
     cudaFree(d_status);
     cudaFree(ws);
@@ -159,6 +191,32 @@ struct tcfft_plan_s {
   }
 
   size_t io_bytes() const { return (size_t)points * 4u * (split ? 2u : 1u); }
+
+  std::map<int, float*> stage_tables;  // by number of radix-16 stages
+
+  tcfft_status stage_table(int S, const float** out) {
+    auto it = stage_tables.find(S);
+    if (it != stage_tables.end()) {
+      *out = it->second;
+      return TCFFT_OK;
+    }
+    int rows = 0;
+    for (int j = 1; j < S; ++j) rows += 1 << (4 * (S - j));
+    float* t = nullptr;
+    const size_t bytes = (size_t)std::max(rows, 1) * 4 * sizeof(float);
+    if (cudaMalloc(&t, bytes) != cudaSuccess) return TCFFT_ERR_ALLOC;
+    table_bytes += bytes;
+    if (rows > 0) {
+      stage_twiddle_kernel<<<(rows + 255) / 256, 256>>>(reinterpret_cast<float4*>(t), S, rows);
+      if (cudaGetLastError() != cudaSuccess) {
+        cudaFree(t);
+        return TCFFT_ERR_LAUNCH;
+      }
+    }
+    stage_tables[S] = t;
+    *out = t;
+    return TCFFT_OK;
+  }
 
   tcfft_status table(int log2M, TwTable** out) {
     auto it = tables.find(log2M);
@@ -217,7 +275,9 @@ tcfft_status add_pass(tcfft_plan_s* pl, int64_t L, int64_t T, int64_t I1, int64_
   const int64_t cap = pl->split ? kCapSplit : kCapPlain;
   int64_t C;
   if (mode == kModeContig) {
-    const int64_t target = pl->split ? 4096 : 8192;
+    int64_t target = pl->split ? 4096 : 8192;
+    const int tgt_env = env_int("TCFFT_POINTS_PER_CTA", 0);  // tuning override
+    if (tgt_env >= 2048 && is_pow2(tgt_env)) target = tgt_env;
     C = std::max<int64_t>(1, target / L);
     while (C > 1 && I1 % C != 0) C /= 2;
   } else {
@@ -255,6 +315,10 @@ tcfft_status add_pass(tcfft_plan_s* pl, int64_t L, int64_t T, int64_t I1, int64_
   p.tw_lo = tw->lo;
   p.tw_hi = tw->hi;
   p.tw_log2S = tw->log2S;
+  const float* stw = nullptr;
+  st = pl->stage_table(log2L / 4, &stw);
+  if (st != TCFFT_OK) return st;
+  p.stw = reinterpret_cast<const float4*>(stw);
   p.otw_level = otw_level;
   if (otw_level) {
     TwTable* ot = nullptr;
@@ -271,10 +335,15 @@ tcfft_status add_pass(tcfft_plan_s* pl, int64_t L, int64_t T, int64_t I1, int64_
   p.out_plane = pl->points;
   ps.src = src;
   ps.dst = dst;
-  ps.grid = dim3((unsigned)((T + C - 1) / C));
-  // shared memory: A tiles (x planes), B image(s), barrier words, 1 KB alignment slack;
-  // padded so that shared memory, not TMEM allocation, limits CTAs per SM.
-  size_t smem = 1024 + (size_t)planes * p.tiles * kTileBytes + (size_t)planes * kBImageBytes + 64;
+  p.nchunks = (T + C - 1) / C;
+  // shared memory: A tiles (x planes), raw prefetch buffer (x planes, when it
+  // fits), B image(s), barrier words, 1 KB alignment slack; padded so that
+  // shared memory, not TMEM allocation, limits CTAs per SM.
+  const size_t base = 1024 + (size_t)planes * p.tiles * kTileBytes + (size_t)planes * kBImageBytes + 64;  // + 2 mbarriers, TMEM slot
+  const size_t raw = (size_t)planes * P * 4;
+  p.async_load = (base + raw <= 227 * 1024) ? 1 : 0;
+  if (env_int("TCFFT_SYNC_LOAD", 0)) p.async_load = 0;  // debugging override
+  size_t smem = base + (p.async_load ? raw : 0);
   const int ctas_tmem = 512 / cols;
   const size_t sm_total = 228 * 1024;
   const size_t per_cta_max = sm_total / ctas_tmem - 1024;
@@ -283,6 +352,32 @@ tcfft_status add_pass(tcfft_plan_s* pl, int64_t L, int64_t T, int64_t I1, int64_
   ps.smem = smem;
   if (cudaFuncSetAttribute(ps.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return TCFFT_ERR_CUDA;
+  // ask for the largest shared-memory carveout so that several CTAs fit per SM
+  if (cudaFuncSetAttribute(ps.fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
+    return TCFFT_ERR_CUDA;
+  // CTAs per SM from the kernel's registers, shared memory and threads
+  // (register file allocated per warp in units of 256 registers)
+  int dev = 0, sms = 0, smem_sm = 0, regs_sm = 0, thr_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  cudaFuncAttributes fa0;
+  if (cudaFuncGetAttributes(&fa0, ps.fn) != cudaSuccess) return TCFFT_ERR_CUDA;
+  const int warp_regs = ((fa0.numRegs * 32 + 255) / 256) * 256;
+  const int by_regs = regs_sm / (warp_regs * (kThreads / 32));
+  const int by_smem = smem_sm / (int)(smem + fa0.sharedSizeBytes + 1024);
+  const int by_thr = thr_sm / kThreads;
+  int occ = std::min(by_regs, std::min(by_smem, by_thr));
+  if (occ < 1) return TCFFT_ERR_INVALID_SIZE;
+  occ = std::min(occ, ctas_tmem);
+  const int occ_env = env_int("TCFFT_CTAS_PER_SM", 0);  // tuning override
+  if (occ_env > 0) occ = std::min(occ, occ_env);
+  ps.grid = dim3((unsigned)std::min<int64_t>(p.nchunks, (int64_t)occ * sms));
+  ps.occ = occ;
+  cudaFuncAttributes fa;
+  ps.regs = (cudaFuncGetAttributes(&fa, ps.fn) == cudaSuccess) ? fa.numRegs : -1;
   pl->passes.push_back(ps);
   return TCFFT_OK;
 }
@@ -503,6 +598,31 @@ size_t tcfft_workspace_bytes(tcfft_plan plan) {
 }
 
 int tcfft_plan_num_launches(tcfft_plan plan) { return plan ? (int)plan->passes.size() : 0; }
+
+size_t tcfft_plan_describe(tcfft_plan plan, char* buf, size_t len) {
+  if (!plan) return 0;
+  std::string out = "[";
+  for (size_t i = 0; i < plan->passes.size(); ++i) {
+    const Pass& ps = plan->passes[i];
+    const PassParams& p = ps.p;
+    const char* modes[3] = {"contig", "strided", "contig_to_strided"};
+    const int mode = (p.in_l.es == 1) ? ((p.out_l.es == 1) ? 0 : 2) : 1;
+    char tmp[512];
+    std::snprintf(tmp, sizeof(tmp),
+                  "%s{\"log2n\": %d, \"mode\": \"%s\", \"transforms\": %lld, \"per_cta\": %d, "
+                  "\"tiles\": %d, \"tmem_cols\": %d, \"smem\": %zu, \"async_load\": %d, \"grid\": %u, "
+                  "\"chunks\": %lld, \"out_twiddle\": %d, \"ctas_per_sm\": %d, \"regs\": %d}",
+                  i ? ", " : "", p.log2N, modes[mode], (long long)p.T, 1 << p.log2C, p.tiles, p.tmem_cols,
+                  ps.smem, p.async_load, ps.grid.x, (long long)p.nchunks, p.otw_level, ps.occ, ps.regs);
+    out += tmp;
+  }
+  out += "]";
+  if (buf && len) {
+    std::strncpy(buf, out.c_str(), len - 1);
+    buf[len - 1] = 0;
+  }
+  return out.size() + 1;
+}
 
 const char* tcfft_status_string(tcfft_status s) {
   switch (s) {
