@@ -63,9 +63,15 @@ struct PassCfg {
   static constexpr bool OUT_C = MODE == kModeContig;
   static constexpr bool SPLIT = SPLIT_;
   static constexpr int PLANES = SPLIT ? 2 : 1;
+  // With two or more radix-16 stages the leading radix-RX twiddle W_N^{k0 n'}
+  // is folded out of the load: its factor W_{16 RX}^{k0 n_1} goes into a
+  // per-k0 copy of the stage-1 DFT matrix (every MMA tile then holds one k0)
+  // and its factor W_N^{k0 n^(2)} into the stage-1 epilogue twiddle.
+  static constexpr bool FOLD = S >= 2 && RX > 1;
   // final outputs go straight to global memory when the lanes of a warp hold
-  // consecutive output indices (one or two radix-16 stages, contiguous out)
-  static constexpr bool DIRECT_OUT = OUT_C && S == 2;
+  // consecutive output indices (two radix-16 stages, no leading radix,
+  // contiguous output)
+  static constexpr bool DIRECT_OUT = OUT_C && S == 2 && RX == 1;
   static_assert(S >= 1 && S <= 3, "pass length out of range");
 };
 
@@ -241,9 +247,11 @@ __device__ __forceinline__ void issue_raw_copy(const PassParams& p, uint32_t raw
 }
 
 // Reads the CTA's C transforms, applies the leading radix-RX step (if any)
-// and writes the stage-1 A operand(s).
-//   contiguous input: sub-transform g = c*RX + k0, stage-1 row g*16^{S-1} + n^(2)
-//   strided input:    sub-transform g = k0*C + c, stage-1 row n^(2)*G + g
+// and writes the stage-1 A operand(s).  Sub-transform g = k0*C + c.
+//   contiguous input: stage-1 row g*16^{S-1} + n^(2)
+//   strided input:    stage-1 row (k0*16^{S-1} + n^(2))*C + c
+// (k0 is the slowest row digit, so with FOLD every 128-row tile has one k0).
+// Without FOLD (one radix-16 stage) the twiddle W_N^{k0 n'} is applied here.
 // Source: global memory (SMEM = false; element e of transform c at
 // c*N + e or c + e*es) or the raw shared buffer (SMEM = true; es = C).
 template <class K, bool SMEM>
@@ -319,7 +327,8 @@ __device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, con
 #pragma unroll
         for (int k0 = 0; k0 < RX; ++k0) {
           float2 y = v[k0];
-          if (k0) y = cmulf(y, tw_lookup(p.tw_lo, p.tw_hi, (uint32_t)k0 * npi, K::LOG2N, p.tw_log2S));
+          if (!K::FOLD && k0)
+            y = cmulf(y, tw_lookup(p.tw_lo, p.tw_hi, (uint32_t)k0 * npi, K::LOG2N, p.tw_log2S));
           hv[k0][i] = f2h2(y.x, y.y);
           if constexpr (K::SPLIT) lv[k0][i] = split_lo(y.x, y.y, hv[k0][i]);
         }
@@ -328,7 +337,7 @@ __device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, con
     if constexpr (K::IN_C) {
 #pragma unroll
       for (int k0 = 0; k0 < RX; ++k0) {
-        const uint32_t g = ((uint32_t)c << K::LOG2RX) + k0;
+        const uint32_t g = ((uint32_t)k0 << log2C) + c;
         if constexpr (K::LQ >= 8) {
           const uint32_t m0 = (g << K::LOG2LQ) + (np & (K::LQ - 1));
           const uint32_t n1 = (uint32_t)np >> K::LOG2LQ;
@@ -353,7 +362,7 @@ __device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, con
       const uint32_t nrest = (uint32_t)np & (K::LQ - 1);
 #pragma unroll
       for (int k0 = 0; k0 < RX; ++k0) {
-        const uint32_t m0 = (nrest << (log2C + K::LOG2RX)) + ((uint32_t)k0 << log2C) + c;
+        const uint32_t m0 = ((((uint32_t)k0 << K::LOG2LQ) + nrest) << log2C) + c;
         a_store8c(A, m0, n1, hv[k0]);
         if constexpr (K::SPLIT) a_store8c(Alo, m0, n1, lv[k0]);
       }
@@ -401,8 +410,9 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 1 : 2)
   const int C = 1 << log2C;
   const uint32_t P = (uint32_t)C << LOG2N;  // points per chunk and plane
   uint8_t* RAW = A + K::PLANES * tiles * kTileBytes;
+  constexpr int NB = K::FOLD ? K::RX : 1;  // DFT matrix images per plane
   uint8_t* Bs = RAW + (p.async_load ? K::PLANES * P * 4u : 0u);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(Bs + K::PLANES * kBImageBytes);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Bs + K::PLANES * NB * kBImageBytes);
   uint64_t* lbar = mbar + 1;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
 
@@ -411,11 +421,16 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 1 : 2)
   const int quarter = warp & 3;  // TMEM lane quarter of this warp
   const int half = warp >> 2;    // which tiles this warp takes in the epilogue
 
-  // DFT matrix image(s) -> shared memory
+  // DFT matrix images -> shared memory: hi images k0 = 0..NB-1, then (split)
+  // the lo images; the global table holds 8 hi then 8 lo images.
   {
     const uint4* src = reinterpret_cast<const uint4*>(p.dft_b);
     uint4* dst = reinterpret_cast<uint4*>(Bs);
-    for (int i = tid; i < K::PLANES * kBImageBytes / 16; i += kThreads) dst[i] = __ldg(src + i);
+    constexpr int per = kBImageBytes / 16;
+    for (int i = tid; i < K::PLANES * NB * per; i += kThreads) {
+      const int plane = i / (NB * per), r = i - plane * (NB * per);
+      dst[i] = __ldg(src + plane * 8 * per + r);
+    }
   }
   if (tid == 0) {
     mbar_init(smem_u32(mbar), 1);
@@ -428,7 +443,6 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 1 : 2)
   }
 
   const uint32_t rows_valid = (uint32_t)C << (LOG2N - 4);  // butterflies per stage
-  const uint32_t log2G = (uint32_t)log2C + K::LOG2RX;      // sub-transforms per CTA
   const uint32_t idesc = make_idesc_f16(128, 32, 1, 0);
   const uint32_t a_base = smem_u32(A), b_base = smem_u32(Bs), raw_s = smem_u32(RAW);
   const uint32_t mbar_s = smem_u32(mbar), lbar_s = smem_u32(lbar);
@@ -499,17 +513,19 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 1 : 2)
         for (int t = 0; t < tiles; ++t) {
           const uint32_t a = a_base + t * kTileBytes;
           const uint32_t d = tmem + 32u * t;
-          mma_f16(d, make_smem_desc(a, 4096, 1024, 2), make_smem_desc(b_base, 128, 512, 0), idesc, 0);
+          // stage 1 with FOLD: the DFT matrix of this tile's k0
+          const uint32_t kb = (K::FOLD && j == 1) ? ((uint32_t)(t * 128) >> (log2C + K::LOG2LQ)) : 0u;
+          const uint32_t bb = b_base + kb * kBImageBytes;
+          mma_f16(d, make_smem_desc(a, 4096, 1024, 2), make_smem_desc(bb, 128, 512, 0), idesc, 0);
           mma_f16(d, make_smem_desc(a + 2048, 4096, 1024, 2),
-                  make_smem_desc(b_base + 256, 128, 512, 0), idesc, 1);
+                  make_smem_desc(bb + 256, 128, 512, 0), idesc, 1);
           if constexpr (SPLIT) {
             const uint32_t alo = a + tiles * kTileBytes;
-            const uint32_t blo = b_base + kBImageBytes;
+            const uint32_t blo = bb + NB * kBImageBytes;
             const uint32_t d2 = tmem + 32u * (tiles + t);
-            mma_f16(d2, make_smem_desc(alo, 4096, 1024, 2), make_smem_desc(b_base, 128, 512, 0),
-                    idesc, 0);
+            mma_f16(d2, make_smem_desc(alo, 4096, 1024, 2), make_smem_desc(bb, 128, 512, 0), idesc, 0);
             mma_f16(d2, make_smem_desc(alo + 2048, 4096, 1024, 2),
-                    make_smem_desc(b_base + 256, 128, 512, 0), idesc, 1);
+                    make_smem_desc(bb + 256, 128, 512, 0), idesc, 1);
             mma_f16(d2, make_smem_desc(a, 4096, 1024, 2), make_smem_desc(blo, 128, 512, 0), idesc, 1);
             mma_f16(d2, make_smem_desc(a + 2048, 4096, 1024, 2),
                     make_smem_desc(blo + 256, 128, 512, 0), idesc, 1);
@@ -555,15 +571,21 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 1 : 2)
         // butterfly identity of this row at stage j: sub-transform g, the
         // digits kk = (k_1 .. k_{j-1}) already produced, and nrest = n^(j+1)
         uint32_t g, nrest, kk;
+        uint32_t k0row = 0;  // k0 of the row (stage 1)
         if (j == 1) {
           kk = 0;
+          const uint32_t lk = (uint32_t)log2C + K::LOG2LQ;  // rows per k0
+          k0row = row >> lk;
+          const uint32_t rem = row & ((1u << lk) - 1u);
+          uint32_t c1;
           if constexpr (K::IN_C) {
-            g = row >> K::LOG2LQ;
-            nrest = row & (K::LQ - 1);
+            c1 = rem >> K::LOG2LQ;
+            nrest = rem & (K::LQ - 1);
           } else {
-            nrest = row >> log2G;
-            g = row & ((1u << log2G) - 1u);
+            nrest = rem >> log2C;
+            c1 = rem & ((1u << log2C) - 1u);
           }
+          g = (k0row << log2C) + c1;
         } else {
           const int sj = 4 * (j - 1);
           kk = row & ((1u << sj) - 1u);
@@ -574,25 +596,25 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 1 : 2)
         }
 
         if (!last) {
-          // twiddle W_{L_j}^{k nrest} = w^k, w = W_{L_j}^{nrest}: (w, w^2) read
-          // from the stage table, the pairs (w^{2i}, w^{2i+1}) advanced by w^2
+          // twiddle of output k: a b^k with (a, b) from the stage table:
+          // stage 1: a = W_N^{k0 nrest}, b = W_{L}^{nrest}; stage j >= 2:
+          // a = 1, b = W_{L_j}^{nrest}.  Pairs (a b^{2i}, a b^{2i+1}) are
+          // advanced by b^2 in packed FP32x2 arithmetic.
           {
             int toff = 0;
+            if (j >= 2) toff = K::RX << K::LOG2LQ;
 #pragma unroll
-            for (int i = 1; i < j; ++i) toff += 1 << (4 * (K::S - i));
-            const float4 e = __ldg(p.stw + toff + (int)nrest);
-            float2 c2 = make_float2(1.0f, e.x), d2 = make_float2(0.0f, e.y);  // (w^0, w^1)
-            const float2 sc = make_float2(e.z, e.z), sd = make_float2(e.w, e.w);
-            const float2 snd = make_float2(-e.w, -e.w);
+            for (int i = 2; i < j; ++i) toff += 1 << (4 * (K::S - i));
+            const int ent = toff + (j == 1 ? (int)((k0row << K::LOG2LQ) + nrest) : (int)nrest);
+            const float4 e = __ldg(p.stw + ent);
+            const float2 a = make_float2(e.x, e.y), b = make_float2(e.z, e.w);
+            const float2 ab = cmulf(a, b), b2 = cmulf(b, b);
+            float2 c2 = make_float2(a.x, ab.x), d2 = make_float2(a.y, ab.y);
+            const float2 sc = make_float2(b2.x, b2.x), sd = make_float2(b2.y, b2.y);
+            const float2 snd = make_float2(-b2.y, -b2.y);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-              if (i > 0) cmul2(X[i], Y[i], c2, d2, make_float2(-d2.x, -d2.y));
-              else {
-                // k = 0 is untouched; k = 1 by w
-                const float xr = X[0].y, xi = Y[0].y;
-                X[0].y = fmaf(xr, e.x, -xi * e.y);
-                Y[0].y = fmaf(xr, e.y, xi * e.x);
-              }
+              cmul2(X[i], Y[i], c2, d2, make_float2(-d2.x, -d2.y));
               if (i < 7) {
                 float2 cn = c2, dn = d2;
                 cmul2(cn, dn, sc, sd, snd);
@@ -640,14 +662,8 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 1 : 2)
               x >>= 4;
             }
           }
-          uint32_t c, k0;
-          if constexpr (K::IN_C) {
-            c = g >> K::LOG2RX;
-            k0 = g & (K::RX - 1);
-          } else {
-            k0 = g >> log2C;
-            c = g & ((1u << log2C) - 1u);
-          }
+          const uint32_t k0 = g >> log2C;
+          const uint32_t c = g & ((1u << log2C) - 1u);
           const uint32_t kbase = k0 + (rev << K::LOG2RX);           // output index at k_S = 0
           constexpr uint32_t kstep = (uint32_t)K::LQ << K::LOG2RX;  // output index step per k_S
           if (p.otw_level) {

@@ -97,47 +97,68 @@ __global__ void twiddle_table_kernel(float2* lo, float2* hi, int log2M, int log2
   }
 }
 
-// Per-stage twiddle bases of a pass with S radix-16 stages (L = 16^S): stage
-// j = 1..S-1 owns R_j = 16^{S-j} entries starting at sum_{i<j} R_i; entry
-// nrest holds (w, w^2) as one float4, w = W_{L_j}^{nrest}, L_j = 16^{S-j+1}
-// (FP64 sincospi, rounded once to FP32).  Lanes of a warp read consecutive
-// entries.
-__global__ void stage_twiddle_kernel(float4* out, int S, int rows) {
+// Epilogue twiddles of a pass of length N = RX * 16^S (L = 16^S, LQ = L/16):
+// the twiddle of output k of a butterfly row is a * b^k with one float4
+// entry (a, b) per row key:
+//   stage 1, entry k0 * LQ + nrest (k0 < RX, nrest < LQ):
+//       a = W_N^{k0 nrest}, b = W_L^{nrest}
+//   stage j = 2..S-1, entry RX*LQ + sum_{2<=i<j} 16^{S-i} + nrest:
+//       a = 1, b = W_{L_j}^{nrest}, L_j = 16^{S-j+1}.
+// FP64 sincospi, each value rounded once to FP32.
+__global__ void stage_twiddle_kernel(float4* out, int log2N, int rows) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= rows) return;
-  int j = 1, off = 0;
-  while (j < S - 1 && row >= off + (1 << (4 * (S - j)))) {
-    off += 1 << (4 * (S - j));
-    ++j;
+  const int S = log2N / 4, RX = 1 << (log2N % 4), LQ = 1 << (4 * (S - 1));
+  double ae, an, be, bn;  // exponents e / denominators n of a and b
+  if (row < RX * LQ) {
+    const int k0 = row / LQ, nrest = row % LQ;
+    ae = (double)(k0 * nrest);
+    an = (double)(RX * 16 * LQ);
+    be = (double)nrest;
+    bn = (double)(16 * LQ);
+  } else {
+    int j = 2, off = RX * LQ;
+    while (j < S - 1 && row >= off + (1 << (4 * (S - j)))) {
+      off += 1 << (4 * (S - j));
+      ++j;
+    }
+    ae = 0.0;
+    an = 1.0;
+    be = (double)(row - off);
+    bn = (double)(1 << (4 * (S - j + 1)));
   }
-  const int nrest = row - off;
-  const double Lj = (double)(1 << (4 * (S - j + 1)));
-  double s1, c1, s2, c2;
-  sincospi(-2.0 * (double)nrest / Lj, &s1, &c1);
-  sincospi(-4.0 * (double)nrest / Lj, &s2, &c2);
-  out[row] = make_float4((float)c1, (float)s1, (float)c2, (float)s2);
+  double sa, ca, sb, cb;
+  sincospi(-2.0 * ae / an, &sa, &ca);
+  sincospi(-2.0 * be / bn, &sb, &cb);
+  out[row] = make_float4((float)ca, (float)sa, (float)cb, (float)sb);
 }
 
-// B operand of the radix-16 stage: the real 32 x 32 form of F_16,
+// B operands of the radix-16 stage: the real 32 x 32 form of a complex
+// 16 x 16 matrix M,
 //   B[k][n]: k < 16 -> Re of input k, k >= 16 -> Im of input k-16;
 //            n < 16 -> Re of output n, n >= 16 -> Im of output n-16;
-//   [[Re W, Im W], [-Im W, Re W]] with W = W_16^{l m}.
+//   [[Re M, Im M], [-Im M, Re M]].
+// Image k0 (k0 < RX) holds M[m][l] = W_16^{l m} W_{16 RX}^{k0 m}
+// = W_{16 RX}^{m (RX l + k0)}: the DFT matrix F_16 with the leading-radix
+// twiddle factor of input n_1 = m folded in (image 0 is plain F_16).
 // Stored K-major without swizzle: core matrices of 8 (n) x 8 (k) halves,
-// K-groups 128 B apart, N-groups 512 B apart.  Image 1 (split only) holds the
-// low part fp16((v - hi) * 2^11).
-__global__ void dft_b_kernel(__half* img) {
+// K-groups 128 B apart, N-groups 512 B apart.  Images 0..7 hold the FP16
+// values, images 8..15 the low parts fp16((v - hi) * 2^11) for split precision.
+__global__ void dft_b_kernel(__half* img, int RX) {
+  const int k0 = blockIdx.x;    // one block per image
   const int idx = threadIdx.x;  // 1024 threads: one per (k, n)
   const int k = idx >> 5, n = idx & 31;
   const int m = k & 15, l = n & 15;
+  const int den = 16 * RX;
   double s, c;
-  sincospi(-2.0 * (double)((l * m) & 15) / 16.0, &s, &c);  // W = c + i s
+  sincospi(-2.0 * (double)((m * (RX * l + k0)) % den) / (double)den, &s, &c);  // W = c + i s
   double v;
   if (k < 16) v = (n < 16) ? c : s;
   else v = (n < 16) ? -s : c;
-  const int off = (n >> 3) * 256 + (k >> 3) * 64 + (n & 7) * 8 + (k & 7);  // in halves
+  const int off = k0 * 1024 + (n >> 3) * 256 + (k >> 3) * 64 + (n & 7) * 8 + (k & 7);  // halves
   const __half h = __double2half(v);
   img[off] = h;
-  img[1024 + off] = __float2half_rn((float)((v - (double)__half2float(h)) * 2048.0));
+  img[8 * 1024 + off] = __float2half_rn((float)((v - (double)__half2float(h)) * 2048.0));
 }
 
 // ------------------------------------------------------------- helpers
@@ -169,7 +190,7 @@ struct tcfft_plan_s {
   int64_t points = 0;  // total complex points per plane
   std::vector<Pass> passes;
   std::map<int, TwTable> tables;
-  __half* dft_b = nullptr;
+  std::map<int, __half*> dft_b;  // by leading radix RX
   int* d_status = nullptr;
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -183,7 +204,7 @@ struct tcfft_plan_s {
       cudaFree(kv.second.hi);
     }
     for (auto& kv : stage_tables) cudaFree(kv.second);
-    cudaFree(dft_b);
+    for (auto& kv : dft_b) cudaFree(kv.second);
     cudaFree(d_status);
     cudaFree(ws);
     cudaFree(h_in_dev);
@@ -192,28 +213,50 @@ struct tcfft_plan_s {
 
   size_t io_bytes() const { return (size_t)points * 4u * (split ? 2u : 1u); }
 
-  std::map<int, float*> stage_tables;  // by number of radix-16 stages
+  std::map<int, float*> stage_tables;  // by log2 of the pass length
 
-  tcfft_status stage_table(int S, const float** out) {
-    auto it = stage_tables.find(S);
+  tcfft_status b_images(int RX, const __half** out) {
+    auto it = dft_b.find(RX);
+    if (it != dft_b.end()) {
+      *out = it->second;
+      return TCFFT_OK;
+    }
+    __half* b = nullptr;
+    if (cudaMalloc(&b, 16 * kBImageBytes) != cudaSuccess) return TCFFT_ERR_ALLOC;
+    cudaMemset(b, 0, 16 * kBImageBytes);
+    table_bytes += 16 * kBImageBytes;
+    dft_b_kernel<<<RX, 1024>>>(b, RX);
+    if (cudaGetLastError() != cudaSuccess) {
+      cudaFree(b);
+      return TCFFT_ERR_LAUNCH;
+    }
+    dft_b[RX] = b;
+    *out = b;
+    return TCFFT_OK;
+  }
+
+  tcfft_status stage_table(int log2N, const float** out) {
+    auto it = stage_tables.find(log2N);
     if (it != stage_tables.end()) {
       *out = it->second;
       return TCFFT_OK;
     }
+    const int S = log2N / 4, RX = 1 << (log2N % 4);
     int rows = 0;
-    for (int j = 1; j < S; ++j) rows += 1 << (4 * (S - j));
+    if (S >= 2) rows = RX << (4 * (S - 1));
+    for (int j = 2; j < S; ++j) rows += 1 << (4 * (S - j));
     float* t = nullptr;
     const size_t bytes = (size_t)std::max(rows, 1) * 4 * sizeof(float);
     if (cudaMalloc(&t, bytes) != cudaSuccess) return TCFFT_ERR_ALLOC;
     table_bytes += bytes;
     if (rows > 0) {
-      stage_twiddle_kernel<<<(rows + 255) / 256, 256>>>(reinterpret_cast<float4*>(t), S, rows);
+      stage_twiddle_kernel<<<(rows + 255) / 256, 256>>>(reinterpret_cast<float4*>(t), log2N, rows);
       if (cudaGetLastError() != cudaSuccess) {
         cudaFree(t);
         return TCFFT_ERR_LAUNCH;
       }
     }
-    stage_tables[S] = t;
+    stage_tables[log2N] = t;
     *out = t;
     return TCFFT_OK;
   }
@@ -295,6 +338,17 @@ tcfft_status add_pass(tcfft_plan_s* pl, int64_t L, int64_t T, int64_t I1, int64_
     // bring small transforms up to at least one full MMA tile when possible
     while (C * L < 2048 && I1 % (2 * C) == 0 && 2 * C * L <= cap) C *= 2;
   }
+  // with two or more radix-16 stages and a leading radix, every 128-row
+  // MMA tile must hold one k0: C * 16^{S-1} >= 128
+  const int S = log2L / 4, RX = 1 << (log2L % 4);
+  const bool fold = S >= 2 && RX > 1;
+  if (fold) {
+    const int64_t need = std::max<int64_t>(1, 128 >> (4 * (S - 1)));
+    if (C < need) {
+      if (I1 % need != 0) return TCFFT_ERR_INVALID_SIZE;
+      C = need;
+    }
+  }
   if (C * L > cap) return TCFFT_ERR_INVALID_SIZE;
   const int64_t P = C * L;
   p.log2C = ilog2(C);
@@ -316,9 +370,13 @@ tcfft_status add_pass(tcfft_plan_s* pl, int64_t L, int64_t T, int64_t I1, int64_
   p.tw_hi = tw->hi;
   p.tw_log2S = tw->log2S;
   const float* stw = nullptr;
-  st = pl->stage_table(log2L / 4, &stw);
+  st = pl->stage_table(log2L, &stw);
   if (st != TCFFT_OK) return st;
   p.stw = reinterpret_cast<const float4*>(stw);
+  const __half* bimg = nullptr;
+  st = pl->b_images(1 << (log2L % 4), &bimg);
+  if (st != TCFFT_OK) return st;
+  p.dft_b = reinterpret_cast<const uint16_t*>(bimg);
   p.otw_level = otw_level;
   if (otw_level) {
     TwTable* ot = nullptr;
@@ -329,7 +387,6 @@ tcfft_status add_pass(tcfft_plan_s* pl, int64_t L, int64_t T, int64_t I1, int64_
     p.otw_lo = ot->lo;
     p.otw_hi = ot->hi;
   }
-  p.dft_b = reinterpret_cast<const uint16_t*>(pl->dft_b);
   p.status = pl->d_status;
   p.in_plane = pl->points;
   p.out_plane = pl->points;
@@ -339,7 +396,9 @@ tcfft_status add_pass(tcfft_plan_s* pl, int64_t L, int64_t T, int64_t I1, int64_
   // shared memory: A tiles (x planes), raw prefetch buffer (x planes, when it
   // fits), B image(s), barrier words, 1 KB alignment slack; padded so that
   // shared memory, not TMEM allocation, limits CTAs per SM.
-  const size_t base = 1024 + (size_t)planes * p.tiles * kTileBytes + (size_t)planes * kBImageBytes + 64;  // + 2 mbarriers, TMEM slot
+  const size_t nb = fold ? (size_t)RX : 1;  // DFT matrix images per plane
+  const size_t base = 1024 + (size_t)planes * p.tiles * kTileBytes + (size_t)planes * nb * kBImageBytes +
+                      64;  // + 2 mbarriers, TMEM slot
   const size_t raw = (size_t)planes * P * 4;
   p.async_load = (base + raw <= 227 * 1024) ? 1 : 0;
   if (env_int("TCFFT_SYNC_LOAD", 0)) p.async_load = 0;  // debugging override
@@ -449,9 +508,6 @@ tcfft_status check_device() {
 tcfft_status common_init(tcfft_plan_s* pl) {
   if (cudaMalloc(&pl->d_status, sizeof(int)) != cudaSuccess) return TCFFT_ERR_ALLOC;
   if (cudaMemset(pl->d_status, 0, sizeof(int)) != cudaSuccess) return TCFFT_ERR_CUDA;
-  if (cudaMalloc(&pl->dft_b, 2 * kBImageBytes) != cudaSuccess) return TCFFT_ERR_ALLOC;
-  dft_b_kernel<<<1, 1024>>>(pl->dft_b);
-  if (cudaGetLastError() != cudaSuccess) return TCFFT_ERR_LAUNCH;
   return TCFFT_OK;
 }
 
@@ -592,7 +648,7 @@ size_t tcfft_io_bytes(tcfft_plan plan) { return plan ? plan->io_bytes() : 0; }
 
 size_t tcfft_workspace_bytes(tcfft_plan plan) {
   if (!plan) return 0;
-  size_t b = plan->ws_bytes + plan->table_bytes + 2 * kBImageBytes + sizeof(int);
+  size_t b = plan->ws_bytes + plan->table_bytes + sizeof(int);
   if (plan->h_in_dev) b += 2 * plan->io_bytes();
   return b;
 }
