@@ -1,0 +1,160 @@
+// Launch geometry of fused passes: see pass_setup.h.
+#include "pass_setup.h"
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+
+namespace tcfft {
+
+const void* pass_fn_m0_plain(int log2N);
+const void* pass_fn_m1_plain(int log2N);
+const void* pass_fn_m2_plain(int log2N);
+const void* pass_fn_m0_split(int log2N);
+const void* pass_fn_m1_split(int log2N);
+const void* pass_fn_m2_split(int log2N);
+
+namespace {
+// points per CTA (C * N) limits: shared memory holds 4 B (plain) or 8 B
+// (split) per point and TMEM 32 (plain) or 64 (split) FP32 columns per 2048.
+constexpr int64_t kCapPlain = 32768;
+constexpr int64_t kCapSplit = 16384;
+}  // namespace
+
+int ilog2(int64_t v) {
+  int r = 0;
+  while ((int64_t(1) << r) < v) ++r;
+  return r;
+}
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int env_int(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  return (v && *v) ? std::atoi(v) : dflt;
+}
+
+const void* pass_fn(int log2N, int mode, bool split) {
+  if (log2N < kMinLog2Pass || log2N > max_log2_pass(mode, split)) return nullptr;
+  switch (mode) {
+    case kModeContig: return split ? pass_fn_m0_split(log2N) : pass_fn_m0_plain(log2N);
+    case kModeStrided: return split ? pass_fn_m1_split(log2N) : pass_fn_m1_plain(log2N);
+    default: return split ? pass_fn_m2_split(log2N) : pass_fn_m2_plain(log2N);
+  }
+}
+
+tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int64_t I2, Side in,
+                           Side out, bool split) {
+
+  std::memset(&ps.p, 0, sizeof(ps.p));
+  PassParams& p = ps.p;
+  const int log2L = ilog2(L);
+  p.log2N = log2L;
+  const bool in_contig = in.es == 1, out_contig = out.es == 1;
+  int mode;
+  if (in_contig && out_contig) mode = kModeContig;
+  else if (!in_contig && !out_contig) mode = kModeStrided;
+  else if (in_contig) mode = kModeToStrided;
+  else return TCFFT_ERR_INVALID_SIZE;
+  // layout contract of the kernel (see SideLayout)
+  if ((in_contig && in.s1 != L) || (!in_contig && in.s1 != 1)) return TCFFT_ERR_INVALID_SIZE;
+  if ((out_contig && out.s1 != L) || (!out_contig && out.s1 != 1)) return TCFFT_ERR_INVALID_SIZE;
+  if (in.es * L >= (int64_t(1) << 31) || out.es * L >= (int64_t(1) << 31)) return TCFFT_ERR_INVALID_SIZE;
+  ps.fn = pass_fn(log2L, mode, split);
+  if (!ps.fn) return TCFFT_ERR_INVALID_SIZE;
+  const int64_t cap = split ? kCapSplit : kCapPlain;
+  int64_t C;
+  if (mode == kModeContig) {
+    int64_t target = split ? 4096 : 8192;
+    const int tgt_env = env_int("TCFFT_POINTS_PER_CTA", 0);  // tuning override
+    if (tgt_env >= 2048 && is_pow2(tgt_env)) target = tgt_env;
+    C = std::max<int64_t>(1, target / L);
+    while (C > 1 && I1 % C != 0) C /= 2;
+  } else {
+    // strided side: C adjacent transforms per element index, C | I1, C >= 8
+    const int64_t soft = split ? 8192 : 16384;
+    C = 0;
+    for (int64_t c : {32, 16, 8}) {
+      if (I1 % c == 0 && c * L <= soft) {
+        C = c;
+        break;
+      }
+    }
+    if (C == 0 && I1 % 8 == 0 && 8 * L <= cap) C = 8;
+    if (C == 0) return TCFFT_ERR_INVALID_SIZE;
+    // bring small transforms up to at least one full MMA tile when possible
+    while (C * L < 2048 && I1 % (2 * C) == 0 && 2 * C * L <= cap) C *= 2;
+  }
+  // with two or more radix-16 stages and a leading radix, every 128-row
+  // MMA tile must hold one k0: C * 16^{S-1} >= 128
+  const int S = log2L / 4, RX = 1 << (log2L % 4);
+  const bool fold = S >= 2 && RX > 1;
+  if (fold) {
+    const int64_t need = std::max<int64_t>(1, 128 >> (4 * (S - 1)));
+    if (C < need) {
+      if (I1 % need != 0) return TCFFT_ERR_INVALID_SIZE;
+      C = need;
+    }
+  }
+  if (C * L > cap) return TCFFT_ERR_INVALID_SIZE;
+  const int64_t P = C * L;
+  p.log2C = ilog2(C);
+  p.tiles = (int)((P + 2047) / 2048);
+  const int planes = split ? 2 : 1;
+  int cols = 32;
+  while (cols < 32 * p.tiles * planes) cols *= 2;
+  if (cols > 512) return TCFFT_ERR_INVALID_SIZE;
+  p.tmem_cols = cols;
+  p.T = T;
+  p.log2I1 = ilog2(I1);
+  p.log2I2 = ilog2(I2);
+  p.in_l = SideLayout{in.s1, in.s2, in.s3, (uint32_t)in.es};
+  p.out_l = SideLayout{out.s1, out.s2, out.s3, (uint32_t)out.es};
+  p.nchunks = (T + C - 1) / C;
+  // shared memory: A tiles (x planes), raw prefetch buffer (x planes, when it
+  // fits), B image(s), barrier words, 1 KB alignment slack; padded so that
+  // shared memory, not TMEM allocation, limits CTAs per SM.
+  const size_t nb = fold ? (size_t)RX : 1;  // DFT matrix images per plane
+  const size_t base = 1024 + (size_t)planes * p.tiles * kTileBytes + (size_t)planes * nb * kBImageBytes +
+                      64;  // + 2 mbarriers, TMEM slot
+  const size_t raw = (size_t)planes * P * 4;
+  p.async_load = (base + raw <= 227 * 1024) ? 1 : 0;
+  if (env_int("TCFFT_SYNC_LOAD", 0)) p.async_load = 0;  // debugging override
+  size_t smem = base + (p.async_load ? raw : 0);
+  const int ctas_tmem = 512 / cols;
+  const size_t sm_total = 228 * 1024;
+  const size_t per_cta_max = sm_total / ctas_tmem - 1024;
+  if (smem < per_cta_max) smem = std::min<size_t>(per_cta_max, 227 * 1024);
+  if (smem > 227 * 1024) return TCFFT_ERR_INVALID_SIZE;
+  ps.smem = smem;
+  if (cudaFuncSetAttribute(ps.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return TCFFT_ERR_CUDA;
+  // ask for the largest shared-memory carveout so that several CTAs fit per SM
+  if (cudaFuncSetAttribute(ps.fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
+    return TCFFT_ERR_CUDA;
+  // CTAs per SM from the kernel's registers, shared memory and threads
+  // (register file allocated per warp in units of 256 registers)
+  int dev = 0, sms = 0, smem_sm = 0, regs_sm = 0, thr_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  cudaFuncAttributes fa0;
+  if (cudaFuncGetAttributes(&fa0, ps.fn) != cudaSuccess) return TCFFT_ERR_CUDA;
+  const int warp_regs = ((fa0.numRegs * 32 + 255) / 256) * 256;
+  const int by_regs = regs_sm / (warp_regs * (kThreads / 32));
+  const int by_smem = smem_sm / (int)(smem + fa0.sharedSizeBytes + 1024);
+  const int by_thr = thr_sm / kThreads;
+  int occ = std::min(by_regs, std::min(by_smem, by_thr));
+  if (occ < 1) return TCFFT_ERR_INVALID_SIZE;
+  occ = std::min(occ, ctas_tmem);
+  const int occ_env = env_int("TCFFT_CTAS_PER_SM", 0);  // tuning override
+  if (occ_env > 0) occ = std::min(occ, occ_env);
+  ps.grid = dim3((unsigned)std::min<int64_t>(p.nchunks, (int64_t)occ * sms));
+  ps.occ = occ;
+  cudaFuncAttributes fa;
+  ps.regs = (cudaFuncGetAttributes(&fa, ps.fn) == cudaSuccess) ? fa.numRegs : -1;
+  return TCFFT_OK;
+}
+
+}  // namespace tcfft

@@ -1,0 +1,42 @@
+// Launch geometry of one fused pass (shared by the plan-based C ABI and the
+// allocation-free entry point): kernel choice, transforms per CTA, MMA tiles,
+// TMEM columns, shared memory, CTAs per SM and the persistent grid.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/tcfft.h"
+#include "pass_params.h"
+
+namespace tcfft {
+
+// One side (input or output) of a pass, in complex elements (see SideLayout).
+struct Side {
+  int64_t s1, s2, s3, es;
+};
+
+struct PassLaunch {
+  PassParams p;
+  const void* fn = nullptr;  // kernel entry point
+  dim3 grid;
+  size_t smem = 0;
+  int occ = 0;   // CTAs per SM the grid was sized for
+  int regs = 0;  // registers per thread of the kernel
+};
+
+int ilog2(int64_t v);
+bool is_pow2(int64_t v);
+// Integer from the environment (debugging and tuning overrides), or dflt.
+int env_int(const char* name, int dflt);
+// Kernel entry point for one (length, mode, precision), or null.
+const void* pass_fn(int log2N, int mode, bool split);
+
+// Fills the geometry of a pass computing DFTs of length L on T transforms
+// indexed by (t1 < I1, t2 < I2, t3) with layouts `in` and `out`, and sets
+// the kernel's shared-memory attributes.  Leaves tables, status word,
+// buffers, planes and output twiddle to the caller.  Allocates nothing.
+tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int64_t I2, Side in,
+                           Side out, bool split);
+
+}  // namespace tcfft

@@ -28,25 +28,9 @@
 
 #include "../../include/tcfft.h"
 #include "pass_params.h"
+#include "pass_setup.h"
+#include "tables.cuh"
 
-namespace tcfft {
-const void* pass_fn_m0_plain(int log2N);
-const void* pass_fn_m1_plain(int log2N);
-const void* pass_fn_m2_plain(int log2N);
-const void* pass_fn_m0_split(int log2N);
-const void* pass_fn_m1_split(int log2N);
-const void* pass_fn_m2_split(int log2N);
-
-// kernel entry point for one (length, mode, precision), or null
-static const void* pass_fn(int log2N, int mode, bool split) {
-  if (log2N < kMinLog2Pass || log2N > max_log2_pass(mode, split)) return nullptr;
-  switch (mode) {
-    case kModeContig: return split ? pass_fn_m0_split(log2N) : pass_fn_m0_plain(log2N);
-    case kModeStrided: return split ? pass_fn_m1_split(log2N) : pass_fn_m1_plain(log2N);
-    default: return split ? pass_fn_m2_split(log2N) : pass_fn_m2_plain(log2N);
-  }
-}
-}  // namespace tcfft
 
 using namespace tcfft;
 
@@ -55,8 +39,7 @@ namespace {
 constexpr int64_t kMaxLog2_1D = 24;
 constexpr int64_t kMaxLog2_2D = 13;
 
-// points per CTA (C * N) limits: shared memory holds 4 B (plain) or 8 B
-// (split) per point and TMEM 32 (plain) or 64 (split) FP32 columns per 2048.
+// points per CTA on a strided side (8 transforms per CTA)
 constexpr int64_t kCapPlain = 32768;
 constexpr int64_t kCapSplit = 16384;
 // largest single-pass transform (contiguous side)
@@ -71,109 +54,9 @@ struct TwTable {
   int log2S = 0;
 };
 
-struct Pass {
-  PassParams p;
-  const void* fn;  // kernel entry point
+struct Pass : PassLaunch {
   Buf src, dst;
-  dim3 grid;
-  size_t smem;
-  int occ = 0;   // CTAs per SM the grid was sized for
-  int regs = 0;  // registers per thread of the kernel
 };
-
-// ------------------------------------------------------------- device code
-// W_M^m = exp(-2 pi i m / M) in FP64 (sincospi), rounded once to FP32.
-__global__ void twiddle_table_kernel(float2* lo, float2* hi, int log2M, int log2S) {
-  const int64_t S = int64_t(1) << log2S;
-  const int64_t H = int64_t(1) << (log2M - log2S);
-  const int64_t M = int64_t(1) << log2M;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S + H;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t m = (i < S) ? i : (i - S) * S;  // exponent
-    double s, c;
-    sincospi(-2.0 * (double)m / (double)M, &s, &c);
-    const float2 w = make_float2((float)c, (float)s);
-    if (i < S) lo[i] = w; else hi[i - S] = w;
-  }
-}
-
-// Epilogue twiddles of a pass of length N = RX * 16^S (L = 16^S, LQ = L/16):
-// the twiddle of output k of a butterfly row is a * b^k with one float4
-// entry (a, b) per row key:
-//   stage 1, entry k0 * LQ + nrest (k0 < RX, nrest < LQ):
-//       a = W_N^{k0 nrest}, b = W_L^{nrest}
-//   stage j = 2..S-1, entry RX*LQ + sum_{2<=i<j} 16^{S-i} + nrest:
-//       a = 1, b = W_{L_j}^{nrest}, L_j = 16^{S-j+1}.
-// FP64 sincospi, each value rounded once to FP32.
-__global__ void stage_twiddle_kernel(float4* out, int log2N, int rows) {
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= rows) return;
-  const int S = log2N / 4, RX = 1 << (log2N % 4), LQ = 1 << (4 * (S - 1));
-  double ae, an, be, bn;  // exponents e / denominators n of a and b
-  if (row < RX * LQ) {
-    const int k0 = row / LQ, nrest = row % LQ;
-    ae = (double)(k0 * nrest);
-    an = (double)(RX * 16 * LQ);
-    be = (double)nrest;
-    bn = (double)(16 * LQ);
-  } else {
-    int j = 2, off = RX * LQ;
-    while (j < S - 1 && row >= off + (1 << (4 * (S - j)))) {
-      off += 1 << (4 * (S - j));
-      ++j;
-    }
-    ae = 0.0;
-    an = 1.0;
-    be = (double)(row - off);
-    bn = (double)(1 << (4 * (S - j + 1)));
-  }
-  double sa, ca, sb, cb;
-  sincospi(-2.0 * ae / an, &sa, &ca);
-  sincospi(-2.0 * be / bn, &sb, &cb);
-  out[row] = make_float4((float)ca, (float)sa, (float)cb, (float)sb);
-}
-
-// B operands of the radix-16 stage: the real 32 x 32 form of a complex
-// 16 x 16 matrix M,
-//   B[k][n]: k < 16 -> Re of input k, k >= 16 -> Im of input k-16;
-//            n < 16 -> Re of output n, n >= 16 -> Im of output n-16;
-//   [[Re M, Im M], [-Im M, Re M]].
-// Image k0 (k0 < RX) holds M[m][l] = W_16^{l m} W_{16 RX}^{k0 m}
-// = W_{16 RX}^{m (RX l + k0)}: the DFT matrix F_16 with the leading-radix
-// twiddle factor of input n_1 = m folded in (image 0 is plain F_16).
-// Stored K-major without swizzle: core matrices of 8 (n) x 8 (k) halves,
-// K-groups 128 B apart, N-groups 512 B apart.  Images 0..7 hold the FP16
-// values, images 8..15 the low parts fp16((v - hi) * 2^11) for split precision.
-__global__ void dft_b_kernel(__half* img, int RX) {
-  const int k0 = blockIdx.x;    // one block per image
-  const int idx = threadIdx.x;  // 1024 threads: one per (k, n)
-  const int k = idx >> 5, n = idx & 31;
-  const int m = k & 15, l = n & 15;
-  const int den = 16 * RX;
-  double s, c;
-  sincospi(-2.0 * (double)((m * (RX * l + k0)) % den) / (double)den, &s, &c);  // W = c + i s
-  double v;
-  if (k < 16) v = (n < 16) ? c : s;
-  else v = (n < 16) ? -s : c;
-  const int off = k0 * 1024 + (n >> 3) * 256 + (k >> 3) * 64 + (n & 7) * 8 + (k & 7);  // halves
-  const __half h = __double2half(v);
-  img[off] = h;
-  img[8 * 1024 + off] = __float2half_rn((float)((v - (double)__half2float(h)) * 2048.0));
-}
-
-// ------------------------------------------------------------- helpers
-int ilog2(int64_t v) {
-  int r = 0;
-  while ((int64_t(1) << r) < v) ++r;
-  return r;
-}
-bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
-
-// Integer from the environment (debugging and tuning overrides), or dflt.
-int env_int(const char* name, int dflt) {
-  const char* v = std::getenv(name);
-  return (v && *v) ? std::atoi(v) : dflt;
-}
 
 tcfft_status from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return TCFFT_OK;
@@ -288,83 +171,18 @@ struct tcfft_plan_s {
 
 namespace {
 
-// Describes one side (input or output) of a pass over a set of transforms.
-struct Side {
-  int64_t s1, s2, s3, es;
-};
-
 // Adds one fused pass computing DFTs of length L on T transforms indexed by
 // (t1 < I1, t2 < I2, t3), reading `src` with layout `in` and writing `dst`
 // with layout `out`.  otw_level / log2M: optional output twiddle W_M^{col k}.
 tcfft_status add_pass(tcfft_plan_s* pl, int64_t L, int64_t T, int64_t I1, int64_t I2, Side in,
                       Side out, Buf src, Buf dst, int otw_level, int log2M) {
   Pass ps;
-  std::memset(&ps.p, 0, sizeof(ps.p));
+  tcfft_status st = pass_geometry(ps, L, T, I1, I2, in, out, pl->split);
+  if (st != TCFFT_OK) return st;
   PassParams& p = ps.p;
   const int log2L = ilog2(L);
-  p.log2N = log2L;
-  const bool in_contig = in.es == 1, out_contig = out.es == 1;
-  int mode;
-  if (in_contig && out_contig) mode = kModeContig;
-  else if (!in_contig && !out_contig) mode = kModeStrided;
-  else if (in_contig) mode = kModeToStrided;
-  else return TCFFT_ERR_INVALID_SIZE;
-  // layout contract of the kernel (see SideLayout)
-  if ((in_contig && in.s1 != L) || (!in_contig && in.s1 != 1)) return TCFFT_ERR_INVALID_SIZE;
-  if ((out_contig && out.s1 != L) || (!out_contig && out.s1 != 1)) return TCFFT_ERR_INVALID_SIZE;
-  if (in.es * L >= (int64_t(1) << 31) || out.es * L >= (int64_t(1) << 31)) return TCFFT_ERR_INVALID_SIZE;
-  ps.fn = pass_fn(log2L, mode, pl->split);
-  if (!ps.fn) return TCFFT_ERR_INVALID_SIZE;
-  const int64_t cap = pl->split ? kCapSplit : kCapPlain;
-  int64_t C;
-  if (mode == kModeContig) {
-    int64_t target = pl->split ? 4096 : 8192;
-    const int tgt_env = env_int("TCFFT_POINTS_PER_CTA", 0);  // tuning override
-    if (tgt_env >= 2048 && is_pow2(tgt_env)) target = tgt_env;
-    C = std::max<int64_t>(1, target / L);
-    while (C > 1 && I1 % C != 0) C /= 2;
-  } else {
-    // strided side: C adjacent transforms per element index, C | I1, C >= 8
-    const int64_t soft = pl->split ? 8192 : 16384;
-    C = 0;
-    for (int64_t c : {32, 16, 8}) {
-      if (I1 % c == 0 && c * L <= soft) {
-        C = c;
-        break;
-      }
-    }
-    if (C == 0 && I1 % 8 == 0 && 8 * L <= cap) C = 8;
-    if (C == 0) return TCFFT_ERR_INVALID_SIZE;
-    // bring small transforms up to at least one full MMA tile when possible
-    while (C * L < 2048 && I1 % (2 * C) == 0 && 2 * C * L <= cap) C *= 2;
-  }
-  // with two or more radix-16 stages and a leading radix, every 128-row
-  // MMA tile must hold one k0: C * 16^{S-1} >= 128
-  const int S = log2L / 4, RX = 1 << (log2L % 4);
-  const bool fold = S >= 2 && RX > 1;
-  if (fold) {
-    const int64_t need = std::max<int64_t>(1, 128 >> (4 * (S - 1)));
-    if (C < need) {
-      if (I1 % need != 0) return TCFFT_ERR_INVALID_SIZE;
-      C = need;
-    }
-  }
-  if (C * L > cap) return TCFFT_ERR_INVALID_SIZE;
-  const int64_t P = C * L;
-  p.log2C = ilog2(C);
-  p.tiles = (int)((P + 2047) / 2048);
-  const int planes = pl->split ? 2 : 1;
-  int cols = 32;
-  while (cols < 32 * p.tiles * planes) cols *= 2;
-  if (cols > 512) return TCFFT_ERR_INVALID_SIZE;
-  p.tmem_cols = cols;
-  p.T = T;
-  p.log2I1 = ilog2(I1);
-  p.log2I2 = ilog2(I2);
-  p.in_l = SideLayout{in.s1, in.s2, in.s3, (uint32_t)in.es};
-  p.out_l = SideLayout{out.s1, out.s2, out.s3, (uint32_t)out.es};
   TwTable* tw = nullptr;
-  tcfft_status st = pl->table(log2L, &tw);
+  st = pl->table(log2L, &tw);
   if (st != TCFFT_OK) return st;
   p.tw_lo = tw->lo;
   p.tw_hi = tw->hi;
@@ -392,51 +210,6 @@ tcfft_status add_pass(tcfft_plan_s* pl, int64_t L, int64_t T, int64_t I1, int64_
   p.out_plane = pl->points;
   ps.src = src;
   ps.dst = dst;
-  p.nchunks = (T + C - 1) / C;
-  // shared memory: A tiles (x planes), raw prefetch buffer (x planes, when it
-  // fits), B image(s), barrier words, 1 KB alignment slack; padded so that
-  // shared memory, not TMEM allocation, limits CTAs per SM.
-  const size_t nb = fold ? (size_t)RX : 1;  // DFT matrix images per plane
-  const size_t base = 1024 + (size_t)planes * p.tiles * kTileBytes + (size_t)planes * nb * kBImageBytes +
-                      64;  // + 2 mbarriers, TMEM slot
-  const size_t raw = (size_t)planes * P * 4;
-  p.async_load = (base + raw <= 227 * 1024) ? 1 : 0;
-  if (env_int("TCFFT_SYNC_LOAD", 0)) p.async_load = 0;  // debugging override
-  size_t smem = base + (p.async_load ? raw : 0);
-  const int ctas_tmem = 512 / cols;
-  const size_t sm_total = 228 * 1024;
-  const size_t per_cta_max = sm_total / ctas_tmem - 1024;
-  if (smem < per_cta_max) smem = std::min<size_t>(per_cta_max, 227 * 1024);
-  if (smem > 227 * 1024) return TCFFT_ERR_INVALID_SIZE;
-  ps.smem = smem;
-  if (cudaFuncSetAttribute(ps.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return TCFFT_ERR_CUDA;
-  // ask for the largest shared-memory carveout so that several CTAs fit per SM
-  if (cudaFuncSetAttribute(ps.fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
-    return TCFFT_ERR_CUDA;
-  // CTAs per SM from the kernel's registers, shared memory and threads
-  // (register file allocated per warp in units of 256 registers)
-  int dev = 0, sms = 0, smem_sm = 0, regs_sm = 0, thr_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-  cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
-  cudaFuncAttributes fa0;
-  if (cudaFuncGetAttributes(&fa0, ps.fn) != cudaSuccess) return TCFFT_ERR_CUDA;
-  const int warp_regs = ((fa0.numRegs * 32 + 255) / 256) * 256;
-  const int by_regs = regs_sm / (warp_regs * (kThreads / 32));
-  const int by_smem = smem_sm / (int)(smem + fa0.sharedSizeBytes + 1024);
-  const int by_thr = thr_sm / kThreads;
-  int occ = std::min(by_regs, std::min(by_smem, by_thr));
-  if (occ < 1) return TCFFT_ERR_INVALID_SIZE;
-  occ = std::min(occ, ctas_tmem);
-  const int occ_env = env_int("TCFFT_CTAS_PER_SM", 0);  // tuning override
-  if (occ_env > 0) occ = std::min(occ, occ_env);
-  ps.grid = dim3((unsigned)std::min<int64_t>(p.nchunks, (int64_t)occ * sms));
-  ps.occ = occ;
-  cudaFuncAttributes fa;
-  ps.regs = (cudaFuncGetAttributes(&fa, ps.fn) == cudaSuccess) ? fa.numRegs : -1;
   pl->passes.push_back(ps);
   return TCFFT_OK;
 }
