@@ -112,6 +112,31 @@ int tcfft_plan_num_launches(tcfft_plan plan);
  * description needs, including the NUL; 0 for a NULL plan. */
 size_t tcfft_plan_describe(tcfft_plan plan, char* buf, size_t len);
 
+/* Allocation-free batched 1D transform (no counterpart in the paper).
+ * For callers that cannot allocate device memory when they need a
+ * transform: processes that reserved their whole device-memory budget up
+ * front (a caching allocator or a serving process with a fixed pool), where
+ * an allocation by the library would fail or take memory promised
+ * elsewhere, and loops that must not pay for cudaMalloc / cudaFree, which
+ * may synchronise the device.  Computes the same forward transform as a
+ * plan made by tcfft_plan_1d(n, batch) and run by tcfft_exec, with the
+ * workspace between its two passes, its twiddle tables and its status word
+ * in fixed-size device arrays of the library (held by every GPU that loads
+ * it until the process exits); it allocates nothing.
+ *   n      power of two, 2^15 <= n <= 2^24 (the two-pass lengths)
+ *   batch  >= 1 with n * batch <= 2^24 points (64 MiB workspace); larger
+ *          requests return TCFFT_ERR_INVALID_SIZE
+ *   in/out device buffers of n * batch interleaved FP16 complex values,
+ *          16-byte aligned (in == out allowed); plain FP16 only
+ *   stream cudaStream_t (NULL = legacy default stream); asynchronous.
+ * The first call on a device fills the tables and synchronises that device;
+ * make that first call before recording work on any stream.  Every call
+ * shares the one workspace: calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.  Nothing
+ * needs clearing between calls (each call overwrites the workspace region
+ * it reads).  Device-side wait timeouts of these kernels are not reported. */
+tcfft_status tcfft_exec_1d_noalloc(int64_t n, int64_t batch, const void* in, void* out, void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* tcfft_status_string(tcfft_status status);
 

@@ -45,6 +45,7 @@ _SIG = {
     "tcfft_plan_num_launches": (ctypes.c_int, [_P]),
     "tcfft_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "tcfft_plan_describe": (ctypes.c_size_t, [_P, ctypes.c_char_p, ctypes.c_size_t]),
+    "tcfft_exec_1d_noalloc": (ctypes.c_int, [_I64, _I64, _P, _P, _P]),
 }
 
 _lock = threading.Lock()
@@ -107,6 +108,11 @@ def tcfft_exec(plan: int, in_ptr: int, out_ptr: int, stream: int = 0) -> None:
 
 def tcfft_exec_host(plan: int, host_in: int, host_out: int, stream: int = 0) -> None:
     _check(lib().tcfft_exec_host(plan, host_in, host_out, stream), "tcfft_exec_host")
+
+
+def tcfft_exec_1d_noalloc(n: int, batch: int, in_ptr: int, out_ptr: int, stream: int = 0) -> None:
+    """Allocation-free 1D transform (see include/tcfft.h): no plan, no device allocation."""
+    _check(lib().tcfft_exec_1d_noalloc(n, batch, in_ptr, out_ptr, stream), "tcfft_exec_1d_noalloc")
 
 
 def tcfft_destroy(plan: int) -> None:
