@@ -137,6 +137,13 @@ size_t tcfft_plan_describe(tcfft_plan plan, char* buf, size_t len);
  * it reads).  Device-side wait timeouts of these kernels are not reported. */
 tcfft_status tcfft_exec_1d_noalloc(int64_t n, int64_t batch, const void* in, void* out, void* stream);
 
+/* Failure-path self-test: runs one kernel that waits, with the library's
+ * bounded device-side wait, on a barrier that nothing ever completes, and
+ * returns what the kernel reports -- TCFFT_ERR_TIMEOUT once limit_cycles
+ * (SM clock cycles, <= 4e9) have passed.  The kernel exits normally; the
+ * context stays usable.  Synchronises the device. */
+tcfft_status tcfft_selftest_wait_timeout(long long limit_cycles);
+
 /* Human-readable name of a status code (static string). */
 const char* tcfft_status_string(tcfft_status status);
 

@@ -46,6 +46,7 @@ _SIG = {
     "tcfft_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "tcfft_plan_describe": (ctypes.c_size_t, [_P, ctypes.c_char_p, ctypes.c_size_t]),
     "tcfft_exec_1d_noalloc": (ctypes.c_int, [_I64, _I64, _P, _P, _P]),
+    "tcfft_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_longlong]),
 }
 
 _lock = threading.Lock()

@@ -30,6 +30,7 @@
 #include "pass_params.h"
 #include "pass_setup.h"
 #include "tables.cuh"
+#include "tc_ptx.cuh"
 
 
 using namespace tcfft;
@@ -300,7 +301,37 @@ tcfft_status finish(tcfft_plan_s* pl, tcfft_status st, tcfft_plan* out) {
 
 }  // namespace
 
+namespace {
+// Waits on an mbarrier that no thread or copy ever completes, with the same
+// bounded wait the pass kernels use, and reports the outcome.
+__global__ void wait_timeout_selftest_kernel(long long limit_cycles, int* status) {
+  __shared__ uint64_t bar;
+  const uint32_t b = tcfft::smem_u32(&bar);
+  if (threadIdx.x == 0) tcfft::mbar_init(b, 1);
+  __syncthreads();
+  const bool got = tcfft::mbar_wait_bounded(b, 0, limit_cycles);
+  if (__syncthreads_or(!got) && threadIdx.x == 0) atomicExch(status, kDevErrTimeout);
+}
+}  // namespace
+
 extern "C" {
+
+tcfft_status tcfft_selftest_wait_timeout(long long limit_cycles) {
+  if (limit_cycles < 0 || limit_cycles > 4000000000LL) return TCFFT_ERR_INVALID_VALUE;
+  tcfft_status st = check_device();
+  if (st != TCFFT_OK) return st;
+  int* d = nullptr;
+  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return TCFFT_ERR_ALLOC;
+  int v = 0;
+  cudaMemset(d, 0, sizeof(int));
+  wait_timeout_selftest_kernel<<<1, 32>>>(limit_cycles, d);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&v, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return from_cuda(e);
+  return (tcfft_status)v;
+}
 
 tcfft_status tcfft_plan_1d_ex(tcfft_plan* plan, int64_t n, int64_t batch, tcfft_precision precision,
                               unsigned flags) {

@@ -79,3 +79,76 @@ def test_deterministic_and_batch_independent():
     (o,) = run_plan(plan, [h[4:5]], (1, n))
     plan.destroy()
     assert np.array_equal(si.as_complex128(o)[0], a[4])
+
+
+# --------------------------------------------------------------- full sizes
+def _full_size_rows(shape, batch, seed, split, rows):
+    """Run one plan at a benchmark size; return sampled transforms and their inputs."""
+    import torch
+    import paper_2104_11471_gb300 as tc
+    from gpu_helpers import to_device
+    prec = tc.TCFFT_FP16_SPLIT if split else tc.TCFFT_FP16
+    plan = (tc.Plan.plan_1d(shape[0], batch, prec) if len(shape) == 1
+            else tc.Plan.plan_2d(shape[0], shape[1], batch, prec))
+    pts = int(np.prod(shape))
+    try:
+        rng = np.random.default_rng(seed)
+        if split:
+            hi, lo = si.split_input((batch,) + tuple(shape), seed)
+            x = to_device(np.concatenate([hi.reshape(-1), lo.reshape(-1)]))
+        else:
+            h = si.half_input((batch,) + tuple(shape), seed)
+            x = to_device(h)
+        y = torch.full_like(x, 0x7E00)
+        plan.exec(x, y)
+        torch.cuda.synchronize()
+        assert plan.last_error() == 0
+        pick = sorted(set([0, batch - 1] + list(rng.integers(0, batch, size=rows))))
+        planes = 2 if split else 1
+        yv = y.view(planes, batch, pts * 2)
+        out = []
+        for b in pick:
+            o = yv[:, b].cpu().numpy().view(np.float16).reshape((planes,) + tuple(shape) + (2,))
+            if split:
+                got = si.split_value(o[0], o[1])
+                xin = si.split_value(hi[b], lo[b])
+            else:
+                got = si.as_complex128(o[0])
+                xin = si.as_complex128(h[b])
+            out.append((got, xin))
+        return out
+    finally:
+        plan.destroy()
+
+
+@pytest.mark.parametrize("log2n", [8, 10, 12, 14, 16, 18, 20, 22, 24])
+def test_1d_sweep_full_size_sampled(log2n):
+    # the benchmark's configuration: 2^28 points per exec, batch = 2^28 / N
+    n = 1 << log2n
+    batch = (1 << 28) // n
+    for got, xin in _full_size_rows((n,), batch, si.sweep_seed(log2n), False, rows=2):
+        ref = oracle.fft_batch(xin[None, :])[0]
+        assert np.all(np.isfinite(got))
+        err = oracle.rel_l2(got, ref)
+        assert err <= PLAIN_TOL, f"N=2^{log2n}: rel-L2 {err:.2e}"
+
+
+@pytest.mark.parametrize("side,split", [(256, False), (512, False), (1024, False), (4096, False),
+                                        (8192, False), (256, True), (1024, True), (4096, True),
+                                        (8192, True)])
+def test_2d_full_size_sampled(side, split):
+    batch = (1 << 28) // (side * side)
+    tol = SPLIT_TOL if split else PLAIN_TOL
+    lg = side.bit_length() - 1
+    for got, xin in _full_size_rows((side, side), batch, si.seed_2d(lg), split, rows=1):
+        ref = oracle.fft_2d(xin)
+        assert np.all(np.isfinite(got))
+        err = oracle.rel_l2(got, ref)
+        assert err <= tol, f"2D {side}^2 split={split}: rel-L2 {err:.2e}"
+
+
+def test_max_abs_within_fp16_range_at_2e24():
+    # the largest 1D outputs must stay finite in FP16 (no hidden scaling)
+    n = 1 << 24
+    for got, xin in _full_size_rows((n,), 16, 7, False, rows=0):
+        assert np.max(np.abs(got)) < 65504
