@@ -135,6 +135,26 @@ def oracle_sample(sizes, budget_points: int):
     return total_flops, total_s, min(threads, os.cpu_count() or 1), " ".join(parts)
 
 
+def oracle_sample_2d(sides):
+    """FP64 oracle, one 2D transform per side; returns (flops, seconds, threads, desc)."""
+    import oracle
+    import seeded_inputs as si
+    oracle.build()
+    threads = oracle.default_threads()
+    flops, secs, parts = 0.0, 0.0, []
+    for side in sides:
+        key = ("2d", side)
+        if key not in _ORACLE_INPUTS:
+            _ORACLE_INPUTS[key] = si.as_complex128(si.half_input((side, side), seed=si.seed_2d(side.bit_length() - 1)))
+        x = _ORACLE_INPUTS[key]
+        t0 = time.perf_counter()
+        oracle.fft_2d(x, nthreads=threads)
+        secs += time.perf_counter() - t0
+        flops += 5.0 * side * side * math.log2(side * side)
+        parts.append(f"{side}x{side}x1")
+    return flops, secs, min(threads, os.cpu_count() or 1), " ".join(parts)
+
+
 # ------------------------------------------------------------------ dist
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -169,14 +189,25 @@ def max_over_ranks(v: float, world: int) -> float:
 
 # ------------------------------------------------------------------ arms
 def run_reference(args, world, rank):
+    """The FP64 CPU oracle as it stands, on the host cores; one bounded sample per step."""
     if rank != 0:
         return
     budget = args.cpu_sample_points
+    if args.workload == "2d":
+        sides = [int(x) for x in args.sizes.split(",")] if args.sizes else [256, 512, 1024, 4096, 8192]
+        sample = lambda: oracle_sample_2d(sides)
+        wl = f"2d: sides {sides}, batch=2^{args.log2_points}/side^2, FP16 uniform[-1,1] inputs"
+        sdesc = "FP64 CPU oracle, one transform per side"
+    else:
+        sizes = [int(x) for x in args.sizes.split(",")] if args.sizes else SWEEP
+        sample = lambda: oracle_sample(sizes, budget)
+        wl = f"1d_sweep: N=2^8..2^24 step 2^2, batch=2^{args.log2_points}/N, FP16 uniform[-1,1] inputs"
+        sdesc = f"FP64 CPU oracle, per size max(1, {budget}//N) transforms"
     flops, secs, cores, desc = 0.0, 0.0, 1, ""
     if args.warmup:
-        oracle_sample(SWEEP, budget)  # untimed: builds the oracle, draws the inputs
+        sample()  # untimed: builds the oracle, draws the inputs
     for _ in range(args.steps):
-        f, s, cores, desc = oracle_sample(SWEEP, budget)
+        f, s, cores, desc = sample()
         flops += f
         secs += s
     value = flops / secs / 1e9
@@ -185,13 +216,112 @@ def run_reference(args, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "1d_sweep: N=2^8..2^24 step 2^2, batch=2^28/N, FP16 uniform[-1,1] inputs",
-                   "sample": f"FP64 CPU oracle, per size max(1, {budget}//N) transforms"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": desc},
+        "config": {"workload": wl, "sample": sdesc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+class Entry:
+    """One exec per step: a plan with its device buffers and accounting."""
+
+    def __init__(self, label, plan, x, y, flops, alg_bytes, check):
+        self.label, self.plan, self.x, self.y = label, plan, x, y
+        self.flops, self.alg_bytes, self.check = flops, alg_bytes, check
+
+
+def _half_draw(n_values: int, seed: int):
+    """n_values FP16 numbers uniform in [-1, 1] (re/im interleaved when used as complex)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-1.0, 1.0, size=n_values).astype(np.float16)
+
+
+def _split_draw(n_values: int, seed: int):
+    """(hi, lo) FP16 planes of an FP64 uniform[-1, 1] draw: lo = fp16((v - hi) * 2^11)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    v = rng.uniform(-1.0, 1.0, size=n_values)
+    hi = v.astype(np.float16)
+    lo = ((v - hi.astype(np.float64)) * 2048.0).astype(np.float16)
+    return hi, lo
+
+
+def build_sweep(args, dev, rank):
+    """The 1D sweep: one exec per N = 2^8..2^24 over the same 2^28-point buffers."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_2104_11471_gb300 as tc
+    sizes = [int(s) for s in args.sizes.split(",")] if args.sizes else SWEEP
+    h = _half_draw(2 * POINTS, 1000 + rank)
+    x = torch.from_numpy(h.view(np.uint16)).to(dev)
+    y = torch.empty_like(x)
+    entries = []
+    for lg in sizes:
+        n = 1 << lg
+        b = POINTS // n
+        plan = tc.Plan.plan_1d(n, b)
+
+        def check(y=y, n=n, b=b):
+            row = b // 2  # one transform from the middle of the batch
+            xin = h[row * 2 * n:(row + 1) * 2 * n].astype(np.float64)
+            out = y[row * 2 * n:(row + 1) * 2 * n].cpu().numpy().view(np.float16).astype(np.float64)
+            ref = oracle.fft_batch((xin[0::2] + 1j * xin[1::2])[None, :])[0]
+            return oracle.rel_l2(out[0::2] + 1j * out[1::2], ref)
+        entries.append(Entry(f"1d n={n} batch={b}", plan, x, y, flops_1d(n, b), 8.0 * n * b, check))
+    cfg = {"workload": f"1d_sweep: N=2^8..2^24 step 2^2, batch=2^{args.log2_points}/N, "
+                       "one exec per size per step, uniform[-1,1] seeded inputs",
+           "sizes": [1 << s for s in sizes], "points_per_exec": POINTS, "precision": "plain FP16",
+           "l2": "inputs larger than L2 (1 GiB per exec), no flush"}
+    cpu_sizes = [(1 << s,) for s in sizes]
+    return entries, cfg, cpu_sizes, (h, None)
+
+
+def build_2d(args, dev, rank):
+    """Batched 2D: sides 256, 512, 1024, 4096, 8192, batch = 2^28 / side^2, plain and split."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_2104_11471_gb300 as tc
+    sides = [int(s) for s in args.sizes.split(",")] if args.sizes else [256, 512, 1024, 4096, 8192]
+    hi, lo = _split_draw(2 * POINTS, 2000 + rank)
+    planes = np.concatenate([hi, lo])
+    x = torch.from_numpy(planes.view(np.uint16)).to(dev)
+    y = torch.empty_like(x)
+    entries = []
+    for split in (False, True):
+        for side in sides:
+            b = POINTS // (side * side)
+            prec = tc.TCFFT_FP16_SPLIT if split else tc.TCFFT_FP16
+            plan = tc.Plan.plan_2d(side, side, b, prec)
+            xs = x if split else x[:2 * POINTS]
+            ys = y if split else y[:2 * POINTS]
+
+            def check(y=y, side=side, b=b, split=split):
+                m = side * side
+                row = b // 2
+                sl = slice(row * 2 * m, (row + 1) * 2 * m)
+                xin = hi[sl].astype(np.float64)
+                o_hi = y[sl].cpu().numpy().view(np.float16).astype(np.float64)
+                if split:
+                    xin = xin + lo[sl].astype(np.float64) / 2048.0
+                    o_lo = y[2 * POINTS:][sl].cpu().numpy().view(np.float16).astype(np.float64)
+                    o_hi = o_hi + o_lo / 2048.0
+                z = (xin[0::2] + 1j * xin[1::2]).reshape(side, side)
+                ref = oracle.fft_2d(z)
+                got = (o_hi[0::2] + 1j * o_hi[1::2]).reshape(side, side)
+                return oracle.rel_l2(got, ref)
+            entries.append(Entry(f"2d {side}x{side} batch={b} {'split' if split else 'plain'}", plan, xs, ys,
+                                 5.0 * side * side * math.log2(side * side) * b,
+                                 (16.0 if split else 8.0) * side * side * b, check))
+    cfg = {"workload": f"2d: sides {sides}, batch=2^{args.log2_points}/side^2, plain FP16 and split FP16 "
+                       "(hi + 2^-11 lo), one exec per (side, precision) per step, uniform[-1,1] seeded inputs",
+           "points_per_exec": POINTS, "precision": "plain and split FP16",
+           "l2": "inputs larger than L2 (1-2 GiB per exec), no flush"}
+    cpu_sizes = [(s, s) for s in sides]
+    return entries, cfg, cpu_sizes, (hi, lo)
 
 
 def run_gpu(args, world, rank, local):
@@ -199,42 +329,33 @@ def run_gpu(args, world, rank, local):
     import torch
 
     import paper_2104_11471_gb300 as tc
-    import seeded_inputs as si
 
     tc.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    sizes = [int(s) for s in args.sizes.split(",")] if args.sizes else SWEEP
-    plans = []
-    for lg in sizes:
-        n = 1 << lg
-        plans.append((lg, n, POINTS // n, tc.Plan.plan_1d(n, POINTS // n)))
-    # inputs: one seeded FP16 draw of 2^28 points, resident in HBM (1 GiB)
-    rng = np.random.default_rng(1000 + rank)
-    h = rng.uniform(-1.0, 1.0, size=2 * POINTS).astype(np.float16)
-    x = torch.from_numpy(h.view(np.uint16)).to(dev)
-    y = torch.empty_like(x)
+    build = {"sweep1d": build_sweep, "2d": build_2d}[args.workload]
+    entries, cfg, cpu_sizes, host = build(args, dev, rank)
     stream = torch.cuda.current_stream()
-    launches_per_step = sum(p.num_launches for *_, p in plans)
+    launches_per_step = sum(e.plan.num_launches for e in entries)
 
     def step(events=None):
-        for i, (lg, n, b, p) in enumerate(plans):
+        for i, e in enumerate(entries):
             if events is not None:
                 events[i][0].record(stream)
-            p.exec(x, y, stream)
+            e.plan.exec(e.x, e.y, stream)
             if events is not None:
                 events[i][1].record(stream)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    for *_, p in plans:
-        st = p.last_error()
+    for e in entries:
+        st = e.plan.last_error()
         if st != 0:
-            raise RuntimeError(f"device status {st} in warm-up")
+            raise RuntimeError(f"device status {st} in warm-up ({e.label})")
 
     ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in plans] for _ in range(args.steps)]
+           for _ in entries] for _ in range(args.steps)]
     t_start, t_stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clk = ClockSampler(local)
     barrier(world)
@@ -249,56 +370,64 @@ def run_gpu(args, world, rank, local):
     barrier(world)
     elapsed_ms = t_start.elapsed_time(t_stop)
     elapsed_ms = max_over_ranks(elapsed_ms, world)
-    flops_step = sum(flops_1d(n, b) for _, n, b, _ in plans)
+    flops_step = sum(e.flops for e in entries)
     value = world * flops_step * args.steps / (elapsed_ms / 1e3) / 1e9
+    for e in entries:
+        st = e.plan.last_error()
+        if st != 0:
+            raise RuntimeError(f"device status {st} in timed region ({e.label})")
 
     peak, peak_kind = peaks()
-    per_n = []
+    per = []
     tot_bytes, tot_ms = 0.0, 0.0
-    for i, (lg, n, b, p) in enumerate(plans):
+    for i, e in enumerate(entries):
         ms = [ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps)]
         avg = sum(ms) / len(ms)
-        alg = 8.0 * n * b
-        tot_bytes += alg
+        tot_bytes += e.alg_bytes
         tot_ms += avg
-        per_n.append({"n": n, "batch": b, "launches": p.num_launches, "ms": round(avg, 4),
-                      "passes": [{k: d[k] for k in ("log2n", "mode", "per_cta", "grid", "async_load", "smem", "ctas_per_sm", "regs")}
-                                 for d in p.describe()],
-                      "gflops": round(flops_1d(n, b) / (avg / 1e3) / 1e9, 1),
-                      "alg_gbs": round(alg / (avg / 1e3) / 1e9, 1),
-                      "frac": round(alg / (avg / 1e3) / 1e9 / peak, 4)})
+        gbs = e.alg_bytes / (avg / 1e3) / 1e9
+        per.append({"exec": e.label, "launches": e.plan.num_launches, "ms": round(avg, 4),
+                    "gflops": round(e.flops / (avg / 1e3) / 1e9, 1), "alg_gbs": round(gbs, 1),
+                    "frac": round(gbs / peak, 4),
+                    "passes": [{k: d[k] for k in ("log2n", "mode", "per_cta", "grid", "async_load", "ctas_per_sm")}
+                               for d in e.plan.describe()]})
     achieved = tot_bytes / (tot_ms / 1e3) / 1e9
-    for *_, p in plans:
-        st = p.last_error()
-        if st != 0:
-            raise RuntimeError(f"device status {st} in timed region")
+
+    # accuracy of the timed outputs: one sampled transform per exec vs the FP64 oracle
+    if not args.no_check:
+        for i, e in enumerate(entries):
+            e.plan.exec(e.x, e.y, stream)
+            torch.cuda.synchronize()
+            per[i]["rel_l2"] = float(f"{e.check():.3e}")
 
     # end to end: pinned host buffers through tcfft_exec_host
     e2e = None
     if not args.no_e2e:
-        hin = torch.from_numpy(h.view(np.uint16)).pin_memory()
+        hin = torch.from_numpy(np.concatenate([p for p in host if p is not None]).view(np.uint16)).pin_memory()
         hout = torch.empty_like(hin).pin_memory()
-        for *_, p in plans:
-            p.exec_host(hin, hout, stream)  # warm-up (allocates the plan's device buffers)
+        for e in entries:
+            e.plan.exec_host(hin, hout, stream)  # warm-up (allocates the plan's device buffers)
         barrier(world)
         t0 = time.perf_counter()
         e2e_steps = max(1, min(args.steps, 3))
         for _ in range(e2e_steps):
-            for *_, p in plans:
-                p.exec_host(hin, hout, stream)
+            for e in entries:
+                e.plan.exec_host(hin, hout, stream)
         e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+        io = sum(e.plan.io_bytes for e in entries)
         e2e = {"value": world * flops_step * e2e_steps / e2e_s / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": len(plans) * hin.numel() * 2,
-               "d2h_bytes_per_step": len(plans) * hout.numel() * 2}
+               "h2d_bytes_per_step": io, "d2h_bytes_per_step": io}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        f, s, cores, desc = oracle_sample(sizes, args.cpu_sample_points)
-        cpu = {"value": f / s / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"FP64 oracle, same sizes, per size max(1,{args.cpu_sample_points}//N) transforms: {desc}"}
+        if args.workload == "sweep1d":
+            f, s_, cores, desc = oracle_sample([int(math.log2(c[0])) for c in cpu_sizes], args.cpu_sample_points)
+        else:
+            f, s_, cores, desc = oracle_sample_2d([c[0] for c in cpu_sizes])
+        cpu = {"value": f / s_ / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
 
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic_1d_sweep.json")
+    tpath = os.path.join(ROOT, "profiles", f"traffic_{args.workload}.json")
     if os.path.exists(tpath):
         try:
             with open(tpath) as f:
@@ -307,27 +436,26 @@ def run_gpu(args, world, rank, local):
                 traffic = td.get("traffic_bytes_per_step")
         except Exception:
             traffic = None
-    for *_, p in plans:
-        p.destroy()
+    for e in entries:
+        e.plan.destroy()
     if rank != 0:
         return
+    cfg["parallelism"] = f"replicas x{world}"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
-        "config": {"workload": f"1d_sweep: N=2^8..2^24 step 2^2, batch=2^{args.log2_points}/N, "
-                               "one exec per size per step, uniform[-1,1] seeded inputs",
-                   "sizes": [1 << s for s in sizes], "points_per_exec": POINTS, "precision": "plain FP16",
-                   "l2": "inputs larger than L2 (1 GiB per exec), no flush", "parallelism": f"replicas x{world}"},
+        "config": cfg,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": "pass_kernel (all launches of the step; unit = one exec, 8 B/point)",
+                     "kernel": "pass_kernel (all launches of the step; unit = one exec, 8 B/point plain, "
+                               "16 B/point split)",
                      "peak_kind": peak_kind},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
-        "per_n": per_n,
+        "per_exec": per,
     }
     print(json.dumps(line), flush=True)
 
@@ -356,6 +484,9 @@ def main():
                     help="points per exec (smaller values for profiling captures only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-check", action="store_true", help="skip the sampled oracle check of the outputs")
+    ap.add_argument("--workload", default="sweep1d", choices=["sweep1d", "2d"],
+                    help="sweep1d: the 1D sweep (default); 2d: batched 2D plain and split")
     args = ap.parse_args()
     global POINTS
     POINTS = 1 << args.log2_points
