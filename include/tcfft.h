@@ -59,6 +59,13 @@ typedef enum {
   TCFFT_FP16_SPLIT = 1  /* hi + 2^-11 lo pairs, three MMA products per stage */
 } tcfft_precision;
 
+/* Plan flags (tcfft_plan_*_ex, tcfft_plan_many): */
+#define TCFFT_PLAN_AUTOTUNE 1u /* time candidate CTA geometries per pass at plan
+                                  time; picks are cached in TCFFT_TUNE_CACHE
+                                  (default $HOME/.cache/tcfft_tune.txt) */
+#define TCFFT_PLAN_GRAPH 2u    /* tcfft_exec replays one instantiated CUDA graph
+                                  per (in, out) pair (captured on first use) */
+
 /* Plan a batch of `batch` 1D transforms of length n (the paper's
  * tcfftPlan1D(plan, nx, batch), Sec. 3.1).  Allocates device twiddle tables
  * and, for n > 16384, a workspace of batch*n*4 bytes (x2 for split).  On
@@ -69,11 +76,25 @@ tcfft_status tcfft_plan_1d(tcfft_plan* plan, int64_t n, int64_t batch);
  * (the paper's tcfftPlan2D(plan, nx, ny, batch), Sec. 3.1). */
 tcfft_status tcfft_plan_2d(tcfft_plan* plan, int64_t nx, int64_t ny, int64_t batch);
 
-/* As above with an explicit precision; flags must be 0 (reserved). */
+/* As above with an explicit precision and TCFFT_PLAN_* flags. */
 tcfft_status tcfft_plan_1d_ex(tcfft_plan* plan, int64_t n, int64_t batch,
                               tcfft_precision precision, unsigned flags);
 tcfft_status tcfft_plan_2d_ex(tcfft_plan* plan, int64_t nx, int64_t ny, int64_t batch,
                               tcfft_precision precision, unsigned flags);
+
+/* Ragged batch (many transforms of mixed shapes in one exec): transform i
+ * is 1D of length n0[i] when n1 is NULL or n1[i] == 0, else 2D
+ * n0[i] x n1[i] (row-major, n1[i] contiguous).  The transforms are packed in
+ * one buffer in the given order: transform i starts at element offset
+ * sum_{j<i} size_j (x planes for split precision, each plane holding all
+ * transforms).  Sizes follow the 1D / 2D rules above, except that 2D first
+ * dimensions are limited to 4096 (2048 split).  Transforms of one shape
+ * form a group; each group runs as one batched pass sequence reading and
+ * writing through a device table of transform offsets; with
+ * TCFFT_PLAN_GRAPH the groups are independent branches of one graph launch.
+ * count >= 1. */
+tcfft_status tcfft_plan_many(tcfft_plan* plan, int64_t count, const int64_t* n0, const int64_t* n1,
+                             tcfft_precision precision, unsigned flags);
 
 /* The execution function (Sec. 3.1, Fig. 1): runs the plan's merging
  * kernels in turn on `stream` (a cudaStream_t; NULL = legacy default

@@ -21,6 +21,8 @@ LIB_PATH = os.path.join(_HERE, "libtcfft.so")
 
 TCFFT_FP16 = 0
 TCFFT_FP16_SPLIT = 1
+TCFFT_PLAN_AUTOTUNE = 1
+TCFFT_PLAN_GRAPH = 2
 
 STATUS = {
     0: "TCFFT_OK", 1: "TCFFT_ERR_INVALID_SIZE", 2: "TCFFT_ERR_INVALID_VALUE",
@@ -36,6 +38,7 @@ _SIG = {
     "tcfft_plan_2d": (ctypes.c_int, [ctypes.POINTER(_P), _I64, _I64, _I64]),
     "tcfft_plan_1d_ex": (ctypes.c_int, [ctypes.POINTER(_P), _I64, _I64, ctypes.c_int, ctypes.c_uint]),
     "tcfft_plan_2d_ex": (ctypes.c_int, [ctypes.POINTER(_P), _I64, _I64, _I64, ctypes.c_int, ctypes.c_uint]),
+    "tcfft_plan_many": (ctypes.c_int, [ctypes.POINTER(_P), _I64, _P, _P, ctypes.c_int, ctypes.c_uint]),
     "tcfft_exec": (ctypes.c_int, [_P, _P, _P, _P]),
     "tcfft_exec_host": (ctypes.c_int, [_P, _P, _P, _P]),
     "tcfft_destroy": (ctypes.c_int, [_P]),
@@ -100,6 +103,17 @@ def tcfft_plan_1d(n: int, batch: int, precision: int = TCFFT_FP16, flags: int = 
 def tcfft_plan_2d(nx: int, ny: int, batch: int, precision: int = TCFFT_FP16, flags: int = 0) -> int:
     h = _P()
     _check(lib().tcfft_plan_2d_ex(ctypes.byref(h), nx, ny, batch, precision, flags), "tcfft_plan_2d")
+    return h.value
+
+
+def tcfft_plan_many(shapes, precision: int = TCFFT_FP16, flags: int = 0) -> int:
+    """shapes: sequence of (n,) or (nx, ny) tuples, packed in that order."""
+    cnt = len(shapes)
+    a = (ctypes.c_int64 * cnt)(*[s[0] for s in shapes])
+    b = (ctypes.c_int64 * cnt)(*[(s[1] if len(s) > 1 else 0) for s in shapes])
+    h = _P()
+    _check(lib().tcfft_plan_many(ctypes.byref(h), cnt, ctypes.cast(a, _P), ctypes.cast(b, _P), precision, flags),
+           "tcfft_plan_many")
     return h.value
 
 
@@ -175,12 +189,16 @@ class Plan:
         self.precision = precision
 
     @classmethod
-    def plan_1d(cls, n: int, batch: int, precision: int = TCFFT_FP16) -> "Plan":
-        return cls(tcfft_plan_1d(n, batch, precision), "1d", (n,), batch, precision)
+    def plan_1d(cls, n: int, batch: int, precision: int = TCFFT_FP16, flags: int = 0) -> "Plan":
+        return cls(tcfft_plan_1d(n, batch, precision, flags), "1d", (n,), batch, precision)
 
     @classmethod
-    def plan_2d(cls, nx: int, ny: int, batch: int, precision: int = TCFFT_FP16) -> "Plan":
-        return cls(tcfft_plan_2d(nx, ny, batch, precision), "2d", (nx, ny), batch, precision)
+    def plan_2d(cls, nx: int, ny: int, batch: int, precision: int = TCFFT_FP16, flags: int = 0) -> "Plan":
+        return cls(tcfft_plan_2d(nx, ny, batch, precision, flags), "2d", (nx, ny), batch, precision)
+
+    @classmethod
+    def plan_many(cls, shapes, precision: int = TCFFT_FP16, flags: int = 0) -> "Plan":
+        return cls(tcfft_plan_many(shapes, precision, flags), "many", tuple(shapes), len(shapes), precision)
 
     @property
     def io_bytes(self) -> int:

@@ -93,6 +93,7 @@ __device__ __forceinline__ int64_t side_base(const SideLayout& l, int64_t t, int
                                              int log2I2) {
   const int64_t t1 = t & ((int64_t(1) << log2I1) - 1);
   const int64_t t23 = t >> log2I1;
+  if (l.toff) return t1 * l.s1 + __ldg(l.toff + t23);
   const int64_t t2 = t23 & ((int64_t(1) << log2I2) - 1);
   const int64_t t3 = t23 >> log2I2;
   return t1 * l.s1 + t2 * l.s2 + t3 * l.s3;
@@ -221,14 +222,26 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // the batch are not copied: their rows only feed outputs that are dropped.
 template <class K>
 __device__ __forceinline__ void issue_raw_copy(const PassParams& p, uint32_t raw_s, uint32_t lbar,
-                                               const uint32_t* gin, int log2C, int nvalid) {
+                                               const uint32_t* gin, int64_t t0, int log2C, int nvalid) {
   const uint32_t P = (uint32_t)1 << (log2C + K::LOG2N);
   if constexpr (K::IN_C) {
-    if (threadIdx.x == 0) {
-      const uint32_t bytes = ((uint32_t)nvalid << K::LOG2N) * 4u;
-      mbar_arrive_expect_tx(lbar, bytes * K::PLANES);
-      bulk_g2s(raw_s, gin, bytes, lbar);
-      if constexpr (K::SPLIT) bulk_g2s(raw_s + P * 4u, gin + p.in_plane, bytes, lbar);
+    if (!p.in_gather) {
+      if (threadIdx.x == 0) {
+        const uint32_t bytes = ((uint32_t)nvalid << K::LOG2N) * 4u;
+        mbar_arrive_expect_tx(lbar, bytes * K::PLANES);
+        bulk_g2s(raw_s, gin, bytes, lbar);
+        if constexpr (K::SPLIT) bulk_g2s(raw_s + P * 4u, gin + p.in_plane, bytes, lbar);
+      }
+    } else if (threadIdx.x < 32) {
+      // one bulk copy per transform, from its own offset (ragged batches)
+      const uint32_t bytes = (uint32_t)K::N * 4u;
+      if (threadIdx.x == 0) mbar_arrive_expect_tx(lbar, bytes * K::PLANES * (uint32_t)nvalid);
+      __syncwarp();
+      for (int c = threadIdx.x; c < nvalid; c += 32) {
+        const uint32_t* src = p.in + side_base(p.in_l, t0 + c, p.log2I1, p.log2I2);
+        bulk_g2s(raw_s + (uint32_t)c * bytes, src, bytes, lbar);
+        if constexpr (K::SPLIT) bulk_g2s(raw_s + P * 4u + (uint32_t)c * bytes, src + p.in_plane, bytes, lbar);
+      }
     }
   } else {
     const uint32_t nq = P >> 2;  // 16-byte chunks per plane
@@ -257,7 +270,7 @@ __device__ __forceinline__ void issue_raw_copy(const PassParams& p, uint32_t raw
 template <class K, bool SMEM>
 __device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, const uint32_t* src,
                                             const uint32_t* src_lo, uint32_t es, int log2C,
-                                            int nvalid) {
+                                            int nvalid, int64_t t0 = 0) {
   constexpr int RX = K::RX;
   uint8_t* Alo = A + p.tiles * kTileBytes;
   const int C = 1 << log2C;
@@ -273,7 +286,15 @@ __device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, con
       np = (it & ((1 << BLOG) - 1)) << 3;
       off0 = ((uint32_t)c << K::LOG2N) + np;
       step = K::L;
-      if constexpr (!SMEM) valid = c < nvalid;
+      if constexpr (!SMEM) {
+        valid = c < nvalid;
+        if (p.in_gather && valid) {
+          // ragged batch read from global memory: transform c has its own offset
+          src = p.in + side_base(p.in_l, t0 + c, p.log2I1, p.log2I2);
+          src_lo = src + p.in_plane;
+          off0 = np;
+        }
+      }
     } else {
       const int cbm = (1 << (log2C - 3)) - 1;
       c = (it & cbm) << 3;
@@ -465,7 +486,7 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 1 : 2)
 
   int64_t chunk = blockIdx.x;
   if (p.async_load && chunk < p.nchunks) {
-    issue_raw_copy<K>(p, raw_s, lbar_s, chunk_in(chunk), log2C, chunk_valid(chunk));
+    issue_raw_copy<K>(p, raw_s, lbar_s, chunk_in(chunk), chunk << log2C, log2C, chunk_valid(chunk));
     pending = K::IN_C;
   }
 
@@ -494,12 +515,12 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 1 : 2)
       __syncthreads();  // raw buffer consumed: prefetch the next chunk into it
       const int64_t next = chunk + gridDim.x;
       if (next < p.nchunks) {
-        issue_raw_copy<K>(p, raw_s, lbar_s, chunk_in(next), log2C, chunk_valid(next));
+        issue_raw_copy<K>(p, raw_s, lbar_s, chunk_in(next), next << log2C, log2C, chunk_valid(next));
         pending = K::IN_C;
       }
     } else {
       const uint32_t* gin = chunk_in(chunk);
-      load_stage1<K, false>(p, A, gin, gin + p.in_plane, p.in_l.es, log2C, nvalid);
+      load_stage1<K, false>(p, A, gin, gin + p.in_plane, p.in_l.es, log2C, nvalid, t0);
     }
 
     fence_proxy_async_smem();
@@ -693,7 +714,8 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 1 : 2)
           if constexpr (K::DIRECT_OUT) {
             // lanes hold consecutive output indices: store straight to global
             if ((int)c < nvalid) {
-              uint32_t* o = gout + (c << LOG2N) + kbase;
+              uint32_t* o = (p.out_scatter ? p.out + side_base(p.out_l, t0 + c, p.log2I1, p.log2I2)
+                                           : gout + (c << LOG2N)) + kbase;
 #pragma unroll
               for (int i = 0; i < 8; ++i) {
                 const uint32_t h0 = f2h2(X[i].x, Y[i].x), h1 = f2h2(X[i].y, Y[i].y);
@@ -741,8 +763,10 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 1 : 2)
           const uint32_t c = (q << 2) >> LOG2N;
           const uint32_t ko = (q << 2) & (K::N - 1);
           const uint32_t pq = q ^ stg_key<K>(c, ko, log2C);
-          *reinterpret_cast<uint4*>(gout + (q << 2)) = stg[pq];
-          if constexpr (SPLIT) *reinterpret_cast<uint4*>(gout + p.out_plane + (q << 2)) = stg[nch + pq];
+          uint32_t* o = p.out_scatter ? p.out + side_base(p.out_l, t0 + c, p.log2I1, p.log2I2) + ko
+                                      : gout + (q << 2);
+          *reinterpret_cast<uint4*>(o) = stg[pq];
+          if constexpr (SPLIT) *reinterpret_cast<uint4*>(o + p.out_plane) = stg[nch + pq];
         }
       } else {
         const int cq = log2C - 2;  // log2 of the chunks per output element index

@@ -14,9 +14,14 @@ namespace tcfft {
 // C*N elements); otherwise it is "strided" (s1 == 1: element e of the CTA's
 // C transforms is one run of C adjacent complex values).  The C transforms
 // of a CTA never straddle a t1 run (C divides I1).
+// With a transform-offset table (toff != null) the t2/t3 part of the first
+// element is toff[t >> log2I1] instead: transforms of a ragged batch sit at
+// arbitrary 16-byte-aligned offsets of one buffer.  With I1 == 1 on a
+// contiguous side every transform of a CTA has its own offset ("gather").
 struct SideLayout {
   int64_t s1, s2, s3;
   uint32_t es;
+  const int64_t* toff;
 };
 
 // Pass modes (input side / output side).
@@ -53,6 +58,8 @@ struct PassParams {
   int otw_log2S;
   const float* otw_lo;
   const float* otw_hi;
+  int in_gather;          // contiguous input, one offset per transform (see SideLayout)
+  int out_scatter;        // contiguous output, one offset per transform
   int async_load;         // 1: prefetch the next chunk with cp.async into a raw buffer
   int64_t nchunks;        // CTA work items: ceil(T / C); CTAs loop over them
   const uint16_t* dft_b;  // radix-16 DFT matrix image(s) in the MMA B layout

@@ -43,7 +43,7 @@ const void* pass_fn(int log2N, int mode, bool split) {
 }
 
 tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int64_t I2, Side in,
-                           Side out, bool split) {
+                           Side out, bool split, int64_t target_points) {
 
   std::memset(&ps.p, 0, sizeof(ps.p));
   PassParams& p = ps.p;
@@ -55,9 +55,13 @@ tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int
   else if (!in_contig && !out_contig) mode = kModeStrided;
   else if (in_contig) mode = kModeToStrided;
   else return TCFFT_ERR_INVALID_SIZE;
-  // layout contract of the kernel (see SideLayout)
-  if ((in_contig && in.s1 != L) || (!in_contig && in.s1 != 1)) return TCFFT_ERR_INVALID_SIZE;
-  if ((out_contig && out.s1 != L) || (!out_contig && out.s1 != 1)) return TCFFT_ERR_INVALID_SIZE;
+  // layout contract of the kernel (see SideLayout); a contiguous side with a
+  // transform-offset table and I1 == 1 gathers/scatters transform by transform
+  const bool in_gather = in_contig && in.toff && I1 == 1;
+  const bool out_scatter = out_contig && out.toff && I1 == 1;
+  if ((in_contig && in.s1 != L && !in_gather) || (!in_contig && in.s1 != 1)) return TCFFT_ERR_INVALID_SIZE;
+  if ((out_contig && out.s1 != L && !out_scatter) || (!out_contig && out.s1 != 1))
+    return TCFFT_ERR_INVALID_SIZE;
   if (in.es * L >= (int64_t(1) << 31) || out.es * L >= (int64_t(1) << 31)) return TCFFT_ERR_INVALID_SIZE;
   ps.fn = pass_fn(log2L, mode, split);
   if (!ps.fn) return TCFFT_ERR_INVALID_SIZE;
@@ -67,11 +71,16 @@ tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int
     int64_t target = split ? 4096 : 8192;
     const int tgt_env = env_int("TCFFT_POINTS_PER_CTA", 0);  // tuning override
     if (tgt_env >= 2048 && is_pow2(tgt_env)) target = tgt_env;
+    if (target_points >= 2048 && is_pow2(target_points)) target = target_points;
     C = std::max<int64_t>(1, target / L);
-    while (C > 1 && I1 % C != 0) C /= 2;
+    if (!(in_gather || out_scatter))
+      while (C > 1 && I1 % C != 0) C /= 2;
   } else {
     // strided side: C adjacent transforms per element index, C | I1, C >= 8
-    const int64_t soft = split ? 8192 : 16384;
+    int64_t soft = split ? 4096 : 8192;
+    const int soft_env = env_int("TCFFT_STRIDED_POINTS", 0);  // tuning override
+    if (soft_env >= 1024 && is_pow2(soft_env)) soft = soft_env;
+    if (target_points >= 1024 && is_pow2(target_points)) soft = target_points;
     C = 0;
     for (int64_t c : {32, 16, 8}) {
       if (I1 % c == 0 && c * L <= soft) {
@@ -91,7 +100,7 @@ tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int
   if (fold) {
     const int64_t need = std::max<int64_t>(1, 128 >> (4 * (S - 1)));
     if (C < need) {
-      if (I1 % need != 0) return TCFFT_ERR_INVALID_SIZE;
+      if (I1 % need != 0 && !(in_gather || out_scatter)) return TCFFT_ERR_INVALID_SIZE;
       C = need;
     }
   }
@@ -107,8 +116,10 @@ tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int
   p.T = T;
   p.log2I1 = ilog2(I1);
   p.log2I2 = ilog2(I2);
-  p.in_l = SideLayout{in.s1, in.s2, in.s3, (uint32_t)in.es};
-  p.out_l = SideLayout{out.s1, out.s2, out.s3, (uint32_t)out.es};
+  p.in_l = SideLayout{in.s1, in.s2, in.s3, (uint32_t)in.es, in.toff};
+  p.out_l = SideLayout{out.s1, out.s2, out.s3, (uint32_t)out.es, out.toff};
+  p.in_gather = in_gather;
+  p.out_scatter = out_scatter;
   p.nchunks = (T + C - 1) / C;
   // shared memory: A tiles (x planes), raw prefetch buffer (x planes, when it
   // fits), B image(s), barrier words, 1 KB alignment slack; padded so that
@@ -126,7 +137,9 @@ tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int
   if (smem < per_cta_max) smem = std::min<size_t>(per_cta_max, 227 * 1024);
   if (smem > 227 * 1024) return TCFFT_ERR_INVALID_SIZE;
   ps.smem = smem;
-  if (cudaFuncSetAttribute(ps.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  // the attribute is a per-kernel upper bound shared by every pass (and plan)
+  // that launches this kernel: always the largest, never the pass's own size
+  if (cudaFuncSetAttribute(ps.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
     return TCFFT_ERR_CUDA;
   // ask for the largest shared-memory carveout so that several CTAs fit per SM
   if (cudaFuncSetAttribute(ps.fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)

@@ -14,6 +14,7 @@ namespace tcfft {
 // One side (input or output) of a pass, in complex elements (see SideLayout).
 struct Side {
   int64_t s1, s2, s3, es;
+  const int64_t* toff = nullptr;  // optional transform-offset table (device)
 };
 
 struct PassLaunch {
@@ -36,7 +37,9 @@ const void* pass_fn(int log2N, int mode, bool split);
 // indexed by (t1 < I1, t2 < I2, t3) with layouts `in` and `out`, and sets
 // the kernel's shared-memory attributes.  Leaves tables, status word,
 // buffers, planes and output twiddle to the caller.  Allocates nothing.
+// target_points (0 = default) overrides the points per CTA aimed at: the
+// transforms-per-CTA target of contiguous passes, the cap of strided ones.
 tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int64_t I2, Side in,
-                           Side out, bool split);
+                           Side out, bool split, int64_t target_points = 0);
 
 }  // namespace tcfft

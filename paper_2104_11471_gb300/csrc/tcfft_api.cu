@@ -14,6 +14,7 @@
 //    stride ny), the latter split in two passes as above for large nx.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <sys/stat.h>
 
 #include <algorithm>
 #include <cmath>
@@ -22,6 +23,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -57,6 +59,14 @@ struct TwTable {
 
 struct Pass : PassLaunch {
   Buf src, dst;
+  int64_t src_off = 0, dst_off = 0;  // element offsets into the workspace
+  int group = 0;                     // independent branch of a ragged plan
+};
+
+struct GraphEntry {
+  const void* in;
+  void* out;
+  cudaGraphExec_t exec;
 };
 
 tcfft_status from_cuda(cudaError_t e) {
@@ -81,8 +91,17 @@ struct tcfft_plan_s {
   void* h_in_dev = nullptr;
   void* h_out_dev = nullptr;
   size_t table_bytes = 0;
+  bool autotune = false;              // time candidate geometries at plan time
+  bool use_graph = false;             // exec replays a captured CUDA graph
+  std::vector<int64_t*> toff_tables;  // device transform-offset tables (ragged)
+  std::vector<GraphEntry> graphs;     // instantiated graphs by (in, out)
+  void* tune_buf = nullptr;           // scratch for autotuning
+  size_t tune_bytes = 0;
 
   ~tcfft_plan_s() {
+    for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
+    for (auto* t : toff_tables) cudaFree(t);
+    cudaFree(tune_buf);
     for (auto& kv : tables) {
       cudaFree(kv.second.lo);
       cudaFree(kv.second.hi);
@@ -175,13 +194,35 @@ namespace {
 // Adds one fused pass computing DFTs of length L on T transforms indexed by
 // (t1 < I1, t2 < I2, t3), reading `src` with layout `in` and writing `dst`
 // with layout `out`.  otw_level / log2M: optional output twiddle W_M^{col k}.
+tcfft_status bind_tables(tcfft_plan_s* pl, Pass& ps, int log2L, int otw_level, int log2M);
+tcfft_status tune_pass(tcfft_plan_s* pl, Pass& ps, int64_t L, int64_t T, int64_t I1, int64_t I2, Side in,
+                       Side out, int otw_level, int log2M);
+
 tcfft_status add_pass(tcfft_plan_s* pl, int64_t L, int64_t T, int64_t I1, int64_t I2, Side in,
-                      Side out, Buf src, Buf dst, int otw_level, int log2M) {
+                      Side out, Buf src, Buf dst, int otw_level, int log2M, int group = 0,
+                      int64_t src_off = 0, int64_t dst_off = 0) {
   Pass ps;
   tcfft_status st = pass_geometry(ps, L, T, I1, I2, in, out, pl->split);
   if (st != TCFFT_OK) return st;
+  ps.src = src;
+  ps.dst = dst;
+  ps.src_off = src_off;
+  ps.dst_off = dst_off;
+  ps.group = group;
+  st = bind_tables(pl, ps, ilog2(L), otw_level, log2M);
+  if (st != TCFFT_OK) return st;
+  if (pl->autotune) {
+    st = tune_pass(pl, ps, L, T, I1, I2, in, out, otw_level, log2M);
+    if (st != TCFFT_OK) return st;
+  }
+  pl->passes.push_back(ps);
+  return TCFFT_OK;
+}
+
+// Points the pass at the plan's tables (generated on first use).
+tcfft_status bind_tables(tcfft_plan_s* pl, Pass& ps, int log2L, int otw_level, int log2M) {
+  tcfft_status st;
   PassParams& p = ps.p;
-  const int log2L = ilog2(L);
   TwTable* tw = nullptr;
   st = pl->table(log2L, &tw);
   if (st != TCFFT_OK) return st;
@@ -209,9 +250,135 @@ tcfft_status add_pass(tcfft_plan_s* pl, int64_t L, int64_t T, int64_t I1, int64_
   p.status = pl->d_status;
   p.in_plane = pl->points;
   p.out_plane = pl->points;
-  ps.src = src;
-  ps.dst = dst;
-  pl->passes.push_back(ps);
+  return TCFFT_OK;
+}
+
+// ------------------------------------------------------------- autotuner
+// Chooses, per pass, the points per CTA (transforms per CTA of contiguous
+// passes, the column-block cap of strided ones) among a few candidates by
+// timing each on scratch memory.  Results are cached in a text file
+// (TCFFT_TUNE_CACHE, default $HOME/.cache/tcfft_tune.txt), one
+// "key target" pair per line; the key names length, layout, precision and
+// the size of the batch.
+std::mutex g_tune_mu;
+std::map<std::string, int64_t> g_tune_cache;
+bool g_tune_loaded = false;
+
+std::string tune_path() {
+  const char* e = std::getenv("TCFFT_TUNE_CACHE");
+  if (e && *e) return e;
+  const char* h = std::getenv("HOME");
+  return std::string(h ? h : "/tmp") + "/.cache/tcfft_tune.txt";
+}
+
+void tune_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  FILE* f = std::fopen(tune_path().c_str(), "r");
+  if (!f) return;
+  char key[128];
+  long long v;
+  while (std::fscanf(f, "%127s %lld", key, &v) == 2) g_tune_cache[key] = v;
+  std::fclose(f);
+}
+
+void tune_store() {
+  const std::string path = tune_path();
+  const size_t slash = path.rfind('/');
+  if (slash != std::string::npos) {
+    const std::string dir = path.substr(0, slash);
+    std::string cmd;  // create the cache directory if missing (mkdir -p semantics)
+    for (size_t i = 1; i <= dir.size(); ++i)
+      if (i == dir.size() || dir[i] == '/') mkdir(dir.substr(0, i).c_str(), 0755);
+  }
+  FILE* f = std::fopen(path.c_str(), "w");
+  if (!f) return;
+  for (auto& kv : g_tune_cache) std::fprintf(f, "%s %lld\n", kv.first.c_str(), (long long)kv.second);
+  std::fclose(f);
+}
+
+tcfft_status tune_pass(tcfft_plan_s* pl, Pass& ps, int64_t L, int64_t T, int64_t I1, int64_t I2, Side in,
+                       Side out, int otw_level, int log2M) {
+  const int mode = (in.es == 1) ? ((out.es == 1) ? 0 : 2) : 1;
+  char key[128];
+  std::snprintf(key, sizeof(key), "L%d_m%d_s%d_T%d_g%d", ilog2(L), mode, pl->split ? 1 : 0, ilog2(T),
+                (in.toff || out.toff) ? 1 : 0);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  tune_load();
+  auto it = g_tune_cache.find(key);
+  int64_t best = -1;
+  if (it != g_tune_cache.end()) {
+    best = it->second;
+  } else {
+    // scratch: one buffer serves as input and output (in place), sized for
+    // the plan's largest buffer; its contents do not matter for timing
+    const size_t need = std::max(pl->io_bytes(), pl->ws_bytes) + 4096;
+    if (pl->tune_bytes < need) {
+      cudaFree(pl->tune_buf);
+      pl->tune_buf = nullptr;
+      pl->tune_bytes = 0;
+      if (cudaMalloc(&pl->tune_buf, need) != cudaSuccess) return TCFFT_ERR_ALLOC;
+      cudaMemset(pl->tune_buf, 0, need);
+      pl->tune_bytes = need;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    for (int64_t cand : {4096, 8192, 16384, 32768}) {
+      Pass c;
+      if (pass_geometry(c, L, T, I1, I2, in, out, pl->split, cand) != TCFFT_OK) continue;
+      c.src = ps.src;
+      c.dst = ps.dst;
+      if (bind_tables(pl, c, ilog2(L), otw_level, log2M) != TCFFT_OK) continue;
+      c.p.in = reinterpret_cast<const uint32_t*>(pl->tune_buf);
+      c.p.out = reinterpret_cast<uint32_t*>(pl->tune_buf);
+      void* args[1] = {&c.p};
+      float ms = 0.0f;
+      bool okc = true;
+      for (int rep = 0; rep < 4 && okc; ++rep) {  // first run is a warm-up
+        cudaEventRecord(e0);
+        okc = cudaLaunchKernel(c.fn, c.grid, dim3(kThreads), args, c.smem, 0) == cudaSuccess;
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (rep > 0) ms += t;
+      }
+      if (okc && ms < best_ms) {
+        best_ms = ms;
+        best = cand;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best < 0) return TCFFT_OK;  // keep the default geometry
+    g_tune_cache[key] = best;
+    tune_store();
+  }
+  Pass c;
+  if (pass_geometry(c, L, T, I1, I2, in, out, pl->split, best) != TCFFT_OK) return TCFFT_OK;
+  const PassParams keep = ps.p;
+  ps.fn = c.fn;
+  ps.grid = c.grid;
+  ps.smem = c.smem;
+  ps.occ = c.occ;
+  ps.regs = c.regs;
+  ps.p = c.p;
+  // tables, buffers and output twiddle stay those of the bound pass
+  ps.p.tw_lo = keep.tw_lo;
+  ps.p.tw_hi = keep.tw_hi;
+  ps.p.tw_log2S = keep.tw_log2S;
+  ps.p.stw = keep.stw;
+  ps.p.dft_b = keep.dft_b;
+  ps.p.otw_level = keep.otw_level;
+  ps.p.otw_log2M = keep.otw_log2M;
+  ps.p.otw_log2S = keep.otw_log2S;
+  ps.p.otw_lo = keep.otw_lo;
+  ps.p.otw_hi = keep.otw_hi;
+  ps.p.status = keep.status;
+  ps.p.in_plane = keep.in_plane;
+  ps.p.out_plane = keep.out_plane;
   return TCFFT_OK;
 }
 
@@ -270,6 +437,80 @@ tcfft_status plan_2d(tcfft_plan_s* pl) {
   return add_pass(pl, N2, B * ny * N1, ny, N1, bi, bo, BUF_WS, BUF_OUT, 0, 0);
 }
 
+// Ragged batch: transform i is 1D of length n0[i] (n1 == null or n1[i] == 0)
+// or 2D n0[i] x n1[i]; its data starts at the sum of the sizes of the
+// transforms before it.  Transforms of one shape form a group with its own
+// offset table; each group's passes gather and scatter through that table,
+// and the groups are independent branches of the plan's graph.
+tcfft_status plan_many(tcfft_plan_s* pl, int64_t count, const int64_t* n0, const int64_t* n1) {
+  std::map<std::pair<int64_t, int64_t>, std::vector<int64_t>> groups;
+  int64_t acc = 0;
+  for (int64_t i = 0; i < count; ++i) {
+    const int64_t a = n0[i], b = n1 ? n1[i] : 0;
+    groups[{a, b}].push_back(acc);
+    acc += b ? a * b : a;
+  }
+  pl->points = acc;
+  const int64_t single = pl->split ? kSingleSplit : kSinglePlain;
+  const int64_t cap = pl->split ? kCapSplit : kCapPlain;
+  bool need_ws = false;
+  for (auto& g : groups)
+    if (g.first.second == 0 && g.first.first > single) need_ws = true;
+  if (need_ws) {
+    pl->ws_bytes = (size_t)acc * 4 * (pl->split ? 2 : 1);
+    if (cudaMalloc(&pl->ws, pl->ws_bytes) != cudaSuccess) {
+      pl->ws = nullptr;
+      return TCFFT_ERR_ALLOC;
+    }
+  }
+  int gid = 0;
+  int64_t ws_off = 0;
+  for (auto& g : groups) {
+    const int64_t a = g.first.first, b = g.first.second;
+    const int64_t k = (int64_t)g.second.size();
+    int64_t* toff = nullptr;
+    if (cudaMalloc(&toff, sizeof(int64_t) * k) != cudaSuccess) return TCFFT_ERR_ALLOC;
+    pl->toff_tables.push_back(toff);
+    if (cudaMemcpy(toff, g.second.data(), sizeof(int64_t) * k, cudaMemcpyHostToDevice) != cudaSuccess)
+      return TCFFT_ERR_CUDA;
+    tcfft_status st;
+    if (b == 0) {
+      const int64_t n = a;
+      if (n <= single) {
+        Side sd{n, 0, 0, 1, toff};
+        st = add_pass(pl, n, k, 1, kNoLevel, sd, sd, BUF_IN, BUF_OUT, 0, 0, gid);
+      } else {
+        const int lg = ilog2(n);
+        const int64_t N1 = int64_t(1) << ((lg + 1) / 2), N2 = n / N1;
+        Side in1{1, 0, 0, N2, toff}, out1{1, n, 0, N2};
+        st = add_pass(pl, N1, k * N2, N2, kNoLevel, in1, out1, BUF_IN, BUF_WS, 1, lg, gid, 0, ws_off);
+        if (st != TCFFT_OK) return st;
+        Side in2{N2, n, 0, 1}, out2{1, 0, 0, N1, toff};
+        st = add_pass(pl, N2, k * N1, N1, kNoLevel, in2, out2, BUF_WS, BUF_OUT, 0, 0, gid, ws_off, 0);
+        ws_off += k * n;
+      }
+    } else {
+      const int64_t nx = a, ny = b;
+      if (8 * nx > cap) return TCFFT_ERR_INVALID_SIZE;  // ragged 2D keeps columns in one pass
+      Side r{ny, 0, 0, 1, toff};
+      st = add_pass(pl, ny, k * nx, nx, kNoLevel, r, r, BUF_IN, BUF_OUT, 0, 0, gid);
+      if (st != TCFFT_OK) return st;
+      Side c{1, 0, 0, ny, toff};
+      st = add_pass(pl, nx, k * ny, ny, kNoLevel, c, c, BUF_OUT, BUF_OUT, 0, 0, gid);
+    }
+    if (st != TCFFT_OK) return st;
+    ++gid;
+  }
+  return TCFFT_OK;
+}
+
+constexpr unsigned kPlanFlags = TCFFT_PLAN_AUTOTUNE | TCFFT_PLAN_GRAPH;
+
+void apply_flags(tcfft_plan_s* pl, unsigned flags) {
+  pl->autotune = (flags & TCFFT_PLAN_AUTOTUNE) || env_int("TCFFT_AUTOTUNE", 0);
+  pl->use_graph = (flags & TCFFT_PLAN_GRAPH) != 0;
+}
+
 tcfft_status check_device() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return TCFFT_ERR_UNSUPPORTED;
@@ -302,6 +543,57 @@ tcfft_status finish(tcfft_plan_s* pl, tcfft_status st, tcfft_plan* out) {
 }  // namespace
 
 namespace {
+// The pass's parameters with the exec's buffers filled in.
+PassParams bound_params(const tcfft_plan_s* plan, const Pass& ps, const void* in, void* out) {
+  PassParams p = ps.p;
+  uint32_t* bufs[3] = {reinterpret_cast<uint32_t*>(const_cast<void*>(in)),
+                       reinterpret_cast<uint32_t*>(out), reinterpret_cast<uint32_t*>(plan->ws)};
+  p.in = bufs[ps.src] + (ps.src == BUF_WS ? ps.src_off : 0);
+  p.out = bufs[ps.dst] + (ps.dst == BUF_WS ? ps.dst_off : 0);
+  return p;
+}
+
+// Replays the plan as one CUDA graph: passes of a group form a chain, the
+// groups of a ragged plan are independent branches that the GPU may run
+// concurrently.  One instantiated graph is kept per (in, out) pair.
+tcfft_status exec_graph(tcfft_plan_s* plan, const void* in, void* out, cudaStream_t s) {
+  for (const GraphEntry& g : plan->graphs)
+    if (g.in == in && g.out == out)
+      return cudaGraphLaunch(g.exec, s) == cudaSuccess ? TCFFT_OK : TCFFT_ERR_LAUNCH;
+  cudaGraph_t graph;
+  if (cudaGraphCreate(&graph, 0) != cudaSuccess) return TCFFT_ERR_CUDA;
+  std::map<int, cudaGraphNode_t> last;  // last node of each group
+  tcfft_status st = TCFFT_OK;
+  for (const Pass& ps : plan->passes) {
+    PassParams p = bound_params(plan, ps, in, out);
+    void* args[1] = {&p};
+    cudaKernelNodeParams kp = {};
+    kp.func = const_cast<void*>(ps.fn);
+    kp.gridDim = ps.grid;
+    kp.blockDim = dim3(kThreads);
+    kp.sharedMemBytes = (unsigned)ps.smem;
+    kp.kernelParams = args;
+    cudaGraphNode_t node;
+    auto it = last.find(ps.group);
+    const cudaGraphNode_t* deps = (it == last.end()) ? nullptr : &it->second;
+    if (cudaGraphAddKernelNode(&node, graph, deps, deps ? 1 : 0, &kp) != cudaSuccess) {
+      st = TCFFT_ERR_CUDA;
+      break;
+    }
+    last[ps.group] = node;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (st == TCFFT_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) st = TCFFT_ERR_CUDA;
+  cudaGraphDestroy(graph);
+  if (st != TCFFT_OK) return st;
+  if (plan->graphs.size() >= 8) {  // keep a few buffer pairs
+    cudaGraphExecDestroy(plan->graphs.front().exec);
+    plan->graphs.erase(plan->graphs.begin());
+  }
+  plan->graphs.push_back(GraphEntry{in, out, exec});
+  return cudaGraphLaunch(exec, s) == cudaSuccess ? TCFFT_OK : TCFFT_ERR_LAUNCH;
+}
+
 // Waits on an mbarrier that no thread or copy ever completes, with the same
 // bounded wait the pass kernels use, and reports the outcome.
 __global__ void wait_timeout_selftest_kernel(long long limit_cycles, int* status) {
@@ -337,7 +629,7 @@ tcfft_status tcfft_plan_1d_ex(tcfft_plan* plan, int64_t n, int64_t batch, tcfft_
                               unsigned flags) {
   if (!plan) return TCFFT_ERR_INVALID_VALUE;
   *plan = nullptr;
-  if (flags != 0 || (precision != TCFFT_FP16 && precision != TCFFT_FP16_SPLIT))
+  if ((flags & ~kPlanFlags) != 0 || (precision != TCFFT_FP16 && precision != TCFFT_FP16_SPLIT))
     return TCFFT_ERR_INVALID_VALUE;
   if (!is_pow2(n) || n < 16 || ilog2(n) > kMaxLog2_1D || batch < 1) return TCFFT_ERR_INVALID_SIZE;
   if (precision == TCFFT_FP16_SPLIT && ilog2(n) > 22) return TCFFT_ERR_INVALID_SIZE;
@@ -351,6 +643,7 @@ tcfft_status tcfft_plan_1d_ex(tcfft_plan* plan, int64_t n, int64_t batch, tcfft_
   pl->batch = batch;
   pl->split = precision == TCFFT_FP16_SPLIT;
   pl->points = n * batch;
+  apply_flags(pl, flags);
   st = common_init(pl);
   if (st == TCFFT_OK) st = plan_1d(pl);
   return finish(pl, st, plan);
@@ -364,7 +657,7 @@ tcfft_status tcfft_plan_2d_ex(tcfft_plan* plan, int64_t nx, int64_t ny, int64_t 
                               tcfft_precision precision, unsigned flags) {
   if (!plan) return TCFFT_ERR_INVALID_VALUE;
   *plan = nullptr;
-  if (flags != 0 || (precision != TCFFT_FP16 && precision != TCFFT_FP16_SPLIT))
+  if ((flags & ~kPlanFlags) != 0 || (precision != TCFFT_FP16 && precision != TCFFT_FP16_SPLIT))
     return TCFFT_ERR_INVALID_VALUE;
   if (!is_pow2(nx) || !is_pow2(ny) || nx < 16 || ny < 16 || ilog2(nx) > kMaxLog2_2D ||
       ilog2(ny) > kMaxLog2_2D || batch < 1)
@@ -380,8 +673,42 @@ tcfft_status tcfft_plan_2d_ex(tcfft_plan* plan, int64_t nx, int64_t ny, int64_t 
   pl->batch = batch;
   pl->split = precision == TCFFT_FP16_SPLIT;
   pl->points = nx * ny * batch;
+  apply_flags(pl, flags);
   st = common_init(pl);
   if (st == TCFFT_OK) st = plan_2d(pl);
+  return finish(pl, st, plan);
+}
+
+tcfft_status tcfft_plan_many(tcfft_plan* plan, int64_t count, const int64_t* n0, const int64_t* n1,
+                             tcfft_precision precision, unsigned flags) {
+  if (!plan) return TCFFT_ERR_INVALID_VALUE;
+  *plan = nullptr;
+  if (!n0 || (flags & ~kPlanFlags) != 0 || (precision != TCFFT_FP16 && precision != TCFFT_FP16_SPLIT))
+    return TCFFT_ERR_INVALID_VALUE;
+  if (count < 1 || count > (int64_t(1) << 24)) return TCFFT_ERR_INVALID_SIZE;
+  int64_t total = 0;
+  for (int64_t i = 0; i < count; ++i) {
+    const int64_t a = n0[i], b = n1 ? n1[i] : 0;
+    if (b == 0) {
+      if (!is_pow2(a) || a < 16 || ilog2(a) > kMaxLog2_1D) return TCFFT_ERR_INVALID_SIZE;
+      if (precision == TCFFT_FP16_SPLIT && ilog2(a) > 22) return TCFFT_ERR_INVALID_SIZE;
+    } else {
+      if (!is_pow2(a) || !is_pow2(b) || a < 16 || b < 16 || ilog2(a) > kMaxLog2_2D || ilog2(b) > kMaxLog2_2D)
+        return TCFFT_ERR_INVALID_SIZE;
+    }
+    total += b ? a * b : a;
+    if (total > (int64_t(1) << 40)) return TCFFT_ERR_INVALID_SIZE;
+  }
+  tcfft_status st = check_device();
+  if (st != TCFFT_OK) return st;
+  tcfft_plan_s* pl = new (std::nothrow) tcfft_plan_s();
+  if (!pl) return TCFFT_ERR_ALLOC;
+  pl->dims = 0;
+  pl->batch = count;
+  pl->split = precision == TCFFT_FP16_SPLIT;
+  apply_flags(pl, flags);
+  st = common_init(pl);
+  if (st == TCFFT_OK) st = plan_many(pl, count, n0, n1);
   return finish(pl, st, plan);
 }
 
@@ -394,14 +721,17 @@ tcfft_status tcfft_exec(tcfft_plan plan, const void* in, void* out, void* stream
   if ((reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(out) & 15))
     return TCFFT_ERR_INVALID_VALUE;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (plan->use_graph) return exec_graph(plan, in, out, s);
   for (const Pass& ps : plan->passes) {
-    PassParams p = ps.p;
-    void* bufs[3] = {const_cast<void*>(in), out, plan->ws};
-    p.in = reinterpret_cast<const uint32_t*>(bufs[ps.src]);
-    p.out = reinterpret_cast<uint32_t*>(bufs[ps.dst]);
+    PassParams p = bound_params(plan, ps, in, out);
     void* args[1] = {&p};
     cudaError_t e = cudaLaunchKernel(ps.fn, ps.grid, dim3(kThreads), args, ps.smem, s);
-    if (e != cudaSuccess) return TCFFT_ERR_LAUNCH;
+    if (e != cudaSuccess) {
+      if (env_int("TCFFT_DEBUG", 0))
+        std::fprintf(stderr, "tcfft_exec: launch of pass (log2n %d, grid %u, smem %zu) failed: %s\n",
+                     ps.p.log2N, ps.grid.x, ps.smem, cudaGetErrorString(e));
+      return TCFFT_ERR_LAUNCH;
+    }
   }
   return TCFFT_OK;
 }

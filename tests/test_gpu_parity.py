@@ -152,3 +152,18 @@ def test_max_abs_within_fp16_range_at_2e24():
     n = 1 << 24
     for got, xin in _full_size_rows((n,), 16, 7, False, rows=0):
         assert np.max(np.abs(got)) < 65504
+
+
+def test_plans_sharing_a_kernel_with_different_shared_memory():
+    # two plans whose passes use the same kernel with different shared-memory
+    # sizes: creating the second must not break launches of the first
+    import torch
+    import paper_2104_11471_gb300 as tc
+    from gpu_helpers import run_plan
+    big = tc.Plan.plan_1d(16, 1024)          # contiguous, 512 transforms per CTA
+    small = tc.Plan.plan_2d(16, 16, 3)       # same length, small row/column blocks
+    h = si.half_input((1024, 16), seed=5)
+    (o,) = run_plan(big, [h], (1024, 16))
+    check_rows(si.as_complex128(o), oracle.fft_batch(si.as_complex128(h)), PLAIN_TOL, "after second plan")
+    big.destroy()
+    small.destroy()
