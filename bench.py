@@ -155,6 +155,26 @@ def oracle_sample_2d(sides):
     return flops, secs, min(threads, os.cpu_count() or 1), " ".join(parts)
 
 
+def oracle_sample_shapes(shapes):
+    """FP64 oracle on a list of 1D (n,) / 2D (nx, ny) shapes; (flops, seconds, threads, desc)."""
+    import numpy as np
+    import oracle
+    import seeded_inputs as si
+    oracle.build()
+    threads = oracle.default_threads()
+    flops, secs = 0.0, 0.0
+    for i, sh in enumerate(shapes):
+        x = si.as_complex128(si.half_input(tuple(sh), seed=4000 + i))
+        t0 = time.perf_counter()
+        if len(sh) == 1:
+            oracle.fft_batch(x[None, :], nthreads=threads)
+        else:
+            oracle.fft_2d(x, nthreads=threads)
+        secs += time.perf_counter() - t0
+        flops += 5.0 * np.prod(sh) * math.log2(np.prod(sh))
+    return flops, secs, min(threads, os.cpu_count() or 1), f"first {len(shapes)} transforms of the ragged list"
+
+
 # ------------------------------------------------------------------ dist
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -324,6 +344,76 @@ def build_2d(args, dev, rank):
     return entries, cfg, cpu_sizes, (hi, lo)
 
 
+def ragged_shapes(seed: int = 4):
+    """The ragged workload: 4096 1D transforms, N = 2^k with k uniform in 8..16
+    (log-uniform N), plus 256 2D transforms with side uniform in
+    {128, 256, 512, 1024}; shuffled into one packed buffer."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    shapes = [(1 << int(k),) for k in rng.integers(8, 17, size=4096)]
+    shapes += [(int(s), int(s)) for s in rng.choice([128, 256, 512, 1024], size=256)]
+    return [shapes[i] for i in rng.permutation(len(shapes))]
+
+
+def build_ragged(args, dev, rank):
+    """One tcfft_plan_many plan over the ragged workload, replayed as one graph
+    launch per step (autotuned geometry); the same plan run with one launch per
+    pass is timed beside it."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_2104_11471_gb300 as tc
+    shapes = ragged_shapes(4 + rank)
+    pts = sum(int(np.prod(sh)) for sh in shapes)
+    h = _half_draw(2 * pts, 4 + rank)
+    x = torch.from_numpy(h.view(np.uint16)).to(dev)
+    y = torch.empty_like(x)
+    flags = tc.TCFFT_PLAN_GRAPH | (0 if args.no_autotune else tc.TCFFT_PLAN_AUTOTUNE)
+    plan = tc.Plan.plan_many(shapes, tc.TCFFT_FP16, flags)
+    flops = sum(5.0 * np.prod(sh) * math.log2(np.prod(sh)) for sh in shapes)
+    offs = np.concatenate([[0], np.cumsum([int(np.prod(sh)) for sh in shapes])])
+
+    def check(y=y):
+        worst = 0.0
+        picks = [i for i, sh in enumerate(shapes) if len(sh) == 2][:2] + \
+                [i for i, sh in enumerate(shapes) if len(sh) == 1][:6]
+        for i in picks:
+            a, b = offs[i], offs[i + 1]
+            xin = h[2 * a:2 * b].astype(np.float64)
+            out = y[2 * a:2 * b].cpu().numpy().view(np.float16).astype(np.float64)
+            z = (xin[0::2] + 1j * xin[1::2]).reshape(shapes[i])
+            g = (out[0::2] + 1j * out[1::2]).reshape(shapes[i])
+            ref = oracle.fft_batch(z) if len(shapes[i]) == 1 else oracle.fft_2d(z)
+            worst = max(worst, oracle.rel_l2(g, ref))
+        return worst
+    entries = [Entry(f"ragged {len(shapes)} transforms, one graph launch", plan, x, y, flops, 8.0 * pts, check)]
+    cfg = {"workload": "ragged: 4096 1D transforms N=2^k, k~U{8..16}, + 256 2D transforms side~U{128,256,512,1024}, "
+                       "shuffled into one packed buffer, one tcfft_plan_many plan replayed as one CUDA graph "
+                       "launch per step, geometry from the plan-time autotuner; uniform[-1,1] seeded inputs",
+           "transforms": len(shapes), "points_per_exec": pts, "precision": "plain FP16",
+           "l2": f"inputs {pts * 4 / 2**20:.0f} MiB per exec (> L2), no flush"}
+
+    def per_size_launches(steps, stream):
+        """The same plan with one launch per pass (no graph)."""
+        p2 = tc.Plan.plan_many(shapes, tc.TCFFT_FP16, 0 if args.no_autotune else tc.TCFFT_PLAN_AUTOTUNE)
+        for _ in range(2):
+            p2.exec(x, y, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            p2.exec(x, y, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        launches = p2.num_launches
+        p2.destroy()
+        return {"ms_per_step": round(ms, 4), "gflops": round(flops / (ms / 1e3) / 1e9, 1),
+                "launches_per_step": launches}
+    cpu_sizes = [sh for sh in shapes[:64]]
+    return entries, cfg, cpu_sizes, (h, None), per_size_launches
+
+
 def run_gpu(args, world, rank, local):
     import numpy as np
     import torch
@@ -333,8 +423,10 @@ def run_gpu(args, world, rank, local):
     tc.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    build = {"sweep1d": build_sweep, "2d": build_2d}[args.workload]
-    entries, cfg, cpu_sizes, host = build(args, dev, rank)
+    build = {"sweep1d": build_sweep, "2d": build_2d, "ragged": build_ragged}[args.workload]
+    built = build(args, dev, rank)
+    entries, cfg, cpu_sizes, host = built[:4]
+    aux = built[4] if len(built) > 4 else None
     stream = torch.cuda.current_stream()
     launches_per_step = sum(e.plan.num_launches for e in entries)
 
@@ -393,6 +485,8 @@ def run_gpu(args, world, rank, local):
                                for d in e.plan.describe()]})
     achieved = tot_bytes / (tot_ms / 1e3) / 1e9
 
+    compare = aux(args.steps, stream) if aux else None
+
     # accuracy of the timed outputs: one sampled transform per exec vs the FP64 oracle
     if not args.no_check:
         for i, e in enumerate(entries):
@@ -422,8 +516,10 @@ def run_gpu(args, world, rank, local):
     if rank == 0 and not args.no_cpu_baseline:
         if args.workload == "sweep1d":
             f, s_, cores, desc = oracle_sample([int(math.log2(c[0])) for c in cpu_sizes], args.cpu_sample_points)
-        else:
+        elif args.workload == "2d":
             f, s_, cores, desc = oracle_sample_2d([c[0] for c in cpu_sizes])
+        else:
+            f, s_, cores, desc = oracle_sample_shapes(cpu_sizes)
         cpu = {"value": f / s_ / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
 
     traffic = None
@@ -457,6 +553,8 @@ def run_gpu(args, world, rank, local):
         "clocks": clocks,
         "per_exec": per,
     }
+    if compare is not None:
+        line["per_size_launches"] = compare
     print(json.dumps(line), flush=True)
 
 
@@ -485,8 +583,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the sampled oracle check of the outputs")
-    ap.add_argument("--workload", default="sweep1d", choices=["sweep1d", "2d"],
-                    help="sweep1d: the 1D sweep (default); 2d: batched 2D plain and split")
+    ap.add_argument("--workload", default="sweep1d", choices=["sweep1d", "2d", "ragged"],
+                    help="sweep1d: the 1D sweep (default); 2d: batched 2D plain and split; "
+                         "ragged: mixed sizes in one graph launch")
+    ap.add_argument("--no-autotune", action="store_true", help="ragged: skip plan-time autotuning")
     args = ap.parse_args()
     global POINTS
     POINTS = 1 << args.log2_points
