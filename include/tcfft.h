@@ -103,6 +103,12 @@ tcfft_status tcfft_plan_many(tcfft_plan* plan, int64_t count, const int64_t* n0,
  * are enqueued. */
 tcfft_status tcfft_exec(tcfft_plan plan, const void* in, void* out, void* stream);
 
+/* As tcfft_exec on the first `batch` transforms only (1 <= batch <= the
+ * planned batch): in/out hold `batch` transforms (split: two planes of
+ * `batch` transforms each).  Lets a resident plan serve requests of any
+ * smaller batch.  Not for ragged plans (TCFFT_ERR_UNSUPPORTED). */
+tcfft_status tcfft_exec_batch(tcfft_plan plan, const void* in, void* out, int64_t batch, void* stream);
+
 /* End-to-end variant for host buffers: copies host_in to a plan-owned
  * device buffer, runs tcfft_exec, copies the result to host_out, all on
  * `stream`, and synchronises the stream before returning.  host_in and

@@ -41,6 +41,7 @@ _SIG = {
     "tcfft_plan_many": (ctypes.c_int, [ctypes.POINTER(_P), _I64, _P, _P, ctypes.c_int, ctypes.c_uint]),
     "tcfft_exec": (ctypes.c_int, [_P, _P, _P, _P]),
     "tcfft_exec_host": (ctypes.c_int, [_P, _P, _P, _P]),
+    "tcfft_exec_batch": (ctypes.c_int, [_P, _P, _P, _I64, _P]),
     "tcfft_destroy": (ctypes.c_int, [_P]),
     "tcfft_plan_last_error": (ctypes.c_int, [_P]),
     "tcfft_io_bytes": (ctypes.c_size_t, [_P]),
@@ -119,6 +120,10 @@ def tcfft_plan_many(shapes, precision: int = TCFFT_FP16, flags: int = 0) -> int:
 
 def tcfft_exec(plan: int, in_ptr: int, out_ptr: int, stream: int = 0) -> None:
     _check(lib().tcfft_exec(plan, in_ptr, out_ptr, stream), "tcfft_exec")
+
+
+def tcfft_exec_batch(plan: int, in_ptr: int, out_ptr: int, batch: int, stream: int = 0) -> None:
+    _check(lib().tcfft_exec_batch(plan, in_ptr, out_ptr, batch, stream), "tcfft_exec_batch")
 
 
 def tcfft_exec_host(plan: int, host_in: int, host_out: int, stream: int = 0) -> None:
@@ -223,6 +228,9 @@ class Plan:
                 if t.numel() * t.element_size() < self.io_bytes:
                     raise ValueError("buffer smaller than the plan's io_bytes")
         tcfft_exec(self.handle, _ptr(inp), _ptr(out), _stream_handle(stream))
+
+    def exec_batch(self, inp, out, batch: int, stream=None) -> None:
+        tcfft_exec_batch(self.handle, _ptr(inp), _ptr(out), batch, _stream_handle(stream))
 
     def exec_host(self, host_in, host_out, stream=None) -> None:
         tcfft_exec_host(self.handle, _ptr(host_in), _ptr(host_out), _stream_handle(stream))

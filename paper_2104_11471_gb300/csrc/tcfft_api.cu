@@ -736,6 +736,31 @@ tcfft_status tcfft_exec(tcfft_plan plan, const void* in, void* out, void* stream
   return TCFFT_OK;
 }
 
+tcfft_status tcfft_exec_batch(tcfft_plan plan, const void* in, void* out, int64_t batch, void* stream) {
+  if (!plan || !in || !out) return TCFFT_ERR_INVALID_VALUE;
+  if (plan->dims == 0) return TCFFT_ERR_UNSUPPORTED;  // ragged plans run as planned
+  if (batch < 1 || batch > plan->batch) return TCFFT_ERR_INVALID_SIZE;
+  if (batch == plan->batch) return tcfft_exec(plan, in, out, stream);
+  if ((reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(out) & 15))
+    return TCFFT_ERR_INVALID_VALUE;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t per = plan->points / plan->batch;  // points of one transform
+  for (const Pass& ps : plan->passes) {
+    PassParams p = bound_params(plan, ps, in, out);
+    // every pass's transforms are the batch's transforms times a fixed count
+    p.T = ps.p.T / plan->batch * batch;
+    const int64_t C = int64_t(1) << p.log2C;
+    p.nchunks = (p.T + C - 1) / C;
+    // user buffers hold `batch` transforms per plane; the workspace keeps its layout
+    if (ps.src != BUF_WS) p.in_plane = per * batch;
+    if (ps.dst != BUF_WS) p.out_plane = per * batch;
+    const dim3 grid((unsigned)std::min<int64_t>(p.nchunks, (int64_t)ps.grid.x));
+    void* args[1] = {&p};
+    if (cudaLaunchKernel(ps.fn, grid, dim3(kThreads), args, ps.smem, s) != cudaSuccess) return TCFFT_ERR_LAUNCH;
+  }
+  return TCFFT_OK;
+}
+
 tcfft_status tcfft_exec_host(tcfft_plan plan, const void* host_in, void* host_out, void* stream) {
   if (!plan || !host_in || !host_out) return TCFFT_ERR_INVALID_VALUE;
   const size_t bytes = plan->io_bytes();

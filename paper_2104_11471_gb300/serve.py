@@ -1,0 +1,247 @@
+"""Continuous-batching FFT server on one GPU.
+
+Requests (a batch of 1D or 2D transforms of one shape and precision) arrive
+over time.  The server keeps one resident plan per (shape, precision), sized
+for the largest merged batch, with its twiddle tables and workspace on the
+device.  A scheduling loop on the host:
+
+* admits arrived requests into a FIFO queue;
+* whenever one of its CUDA streams (slots) has room, takes the oldest queued
+  request plus every other queued request of the same shape and precision
+  (up to the plan's capacity), reserves their input and output memory
+  against the HBM budget, gathers their inputs into one contiguous batch
+  (device-to-device copies) and runs the plan on that batch with
+  tcfft_exec_batch -- so requests that arrive while others run on the GPU
+  join the next batch and their work overlaps on the device;
+* retires finished batches (CUDA events), releasing their memory.
+
+Latency is arrival to completion as seen by the host.  All transform work
+runs in libtcfft's kernels; this module only schedules, allocates and copies.
+"""
+from __future__ import annotations
+
+import math
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import TCFFT_FP16, TCFFT_FP16_SPLIT, Plan
+
+
+@dataclass
+class Request:
+    rid: int
+    t_arrival: float          # seconds from the start of the trace
+    shape: tuple              # (n,) or (nx, ny)
+    batch: int
+    split: bool
+    pool_off: int = 0         # element offset of the input in the device pool
+    t_done: float = -1.0
+    out: object = None        # device tensor view of the result (kept on request)
+
+    @property
+    def points(self) -> int:
+        return int(np.prod(self.shape)) * self.batch
+
+    @property
+    def flops(self) -> float:
+        m = int(np.prod(self.shape))
+        return 5.0 * m * math.log2(m) * self.batch
+
+
+@dataclass
+class _Job:
+    reqs: list
+    key: tuple
+    stream_idx: int
+    event: object
+    nbytes: int
+    buffers: tuple = field(default=())
+
+
+def poisson_trace(rate: float = 2000.0, seconds: float = 10.0, seed: int = 5, max_batch: int = 64,
+                  k1d=(8, 20), k2d=(6, 11)):
+    """The serving workload: Poisson arrivals; each request a batch of 1..64
+    transforms, 50% 1D with N = 2^k (k uniform in k1d), 50% 2D with side 2^k
+    (k uniform in k2d); precision plain / split 50/50."""
+    rng = np.random.default_rng(seed)
+    t, out, rid = 0.0, [], 0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= seconds:
+            break
+        b = int(rng.integers(1, max_batch + 1))
+        if rng.random() < 0.5:
+            shape = (1 << int(rng.integers(k1d[0], k1d[1] + 1)),)
+        else:
+            s = 1 << int(rng.integers(k2d[0], k2d[1] + 1))
+            shape = (s, s)
+        out.append(Request(rid, t, shape, b, bool(rng.random() < 0.5)))
+        rid += 1
+    return out
+
+
+class FFTServer:
+    def __init__(self, hbm_budget: int = 16 << 30, slots: int = 4, depth: int = 2,
+                 job_points: int = 1 << 26, pool_points: int = 1 << 28, seed: int = 5):
+        import torch
+        self.torch = torch
+        self.budget = hbm_budget
+        self.slots = [torch.cuda.Stream() for _ in range(slots)]
+        self.depth = depth                # batches in flight per stream
+        self.job_points = job_points      # merge requests up to this many points
+        self.plans = {}
+        self.in_use = 0
+        self.peak_in_use = 0
+        # seeded input pool on the device (hi plane, lo plane): requests read slices
+        rng = np.random.default_rng(seed)
+        v = rng.uniform(-1.0, 1.0, size=2 * pool_points)
+        hi = v.astype(np.float16)
+        lo = ((v - hi.astype(np.float64)) * 2048.0).astype(np.float16)
+        self.pool_points = pool_points
+        self.pool_hi = torch.from_numpy(hi.view(np.uint16)).cuda()
+        self.pool_lo = torch.from_numpy(lo.view(np.uint16)).cuda()
+        self.pool_host = (hi, lo)
+
+    # ---------------------------------------------------------------- plans
+    def capacity(self, shape) -> int:
+        m = int(np.prod(shape))
+        return max(64, self.job_points // m)
+
+    def plan(self, shape, split: bool) -> Plan:
+        key = (tuple(shape), split)
+        p = self.plans.get(key)
+        if p is None:
+            prec = TCFFT_FP16_SPLIT if split else TCFFT_FP16
+            cap = self.capacity(shape)
+            p = (Plan.plan_1d(shape[0], cap, prec) if len(shape) == 1
+                 else Plan.plan_2d(shape[0], shape[1], cap, prec))
+            self.plans[key] = p
+        return p
+
+    def prewarm(self, requests):
+        for key in sorted({(r.shape, r.split) for r in requests}):
+            self.plan(*key)
+        self.torch.cuda.synchronize()
+
+    def assign_inputs(self, requests, seed: int = 6):
+        rng = np.random.default_rng(seed)
+        for r in requests:
+            if r.points > self.pool_points:
+                raise ValueError("request larger than the input pool")
+            r.pool_off = int(rng.integers(0, self.pool_points - r.points + 1)) & ~3  # 16-byte aligned
+
+    # ---------------------------------------------------------------- loop
+    def _launch(self, group, key, sidx):
+        torch = self.torch
+        shape, split = key
+        m = int(np.prod(shape))
+        total = sum(r.batch for r in group)
+        pts = total * m
+        planes = 2 if split else 1
+        s = self.slots[sidx]
+        with torch.cuda.stream(s):
+            xin = torch.empty(planes * 2 * pts, dtype=torch.uint16, device="cuda")
+            yout = torch.empty_like(xin)
+            off = 0
+            for r in group:  # gather the inputs into one contiguous batch
+                n = 2 * r.points
+                xin[2 * off:2 * off + n].copy_(self.pool_hi[2 * r.pool_off:2 * r.pool_off + n], non_blocking=True)
+                if split:
+                    xin[2 * pts + 2 * off:2 * pts + 2 * off + n].copy_(
+                        self.pool_lo[2 * r.pool_off:2 * r.pool_off + n], non_blocking=True)
+                off += r.points
+            self.plan(shape, split).exec_batch(xin, yout, total, s)
+            ev = torch.cuda.Event()
+            ev.record(s)
+        return _Job(group, key, sidx, ev, 2 * xin.numel() * 2, (xin, yout))
+
+    def run(self, requests, keep_outputs: bool = False, time_limit: float = 600.0):
+        """Serve the trace in real time; returns statistics."""
+        torch = self.torch
+        pending = deque(sorted(requests, key=lambda r: r.t_arrival))
+        queue = deque()
+        inflight = []
+        per_slot = [0] * len(self.slots)
+        batches = 0
+        t0 = time.perf_counter()
+        while pending or queue or inflight:
+            now = time.perf_counter() - t0
+            if now > time_limit:
+                raise RuntimeError("serving loop exceeded its time limit")
+            while pending and pending[0].t_arrival <= now:
+                queue.append(pending.popleft())
+            for job in list(inflight):
+                if job.event.query():
+                    t = time.perf_counter() - t0
+                    m = int(np.prod(job.key[0]))
+                    off = 0
+                    total = sum(r.batch for r in job.reqs)
+                    for r in job.reqs:
+                        r.t_done = t
+                        if keep_outputs:
+                            y = job.buffers[1]
+                            planes = 2 if job.key[1] else 1
+                            yv = y.view(planes, 2 * total * m)
+                            r.out = yv[:, 2 * off:2 * (off + r.points)].clone()
+                        off += r.points
+                    self.in_use -= job.nbytes
+                    per_slot[job.stream_idx] -= 1
+                    inflight.remove(job)
+            launched = False
+            while queue:
+                free = [i for i, c in enumerate(per_slot) if c < self.depth]
+                if not free:
+                    break
+                head = queue[0]
+                key = (head.shape, head.split)
+                cap = self.capacity(head.shape)
+                group, total = [], 0
+                for r in queue:
+                    if (r.shape, r.split) == key and total + r.batch <= cap:
+                        group.append(r)
+                        total += r.batch
+                planes = 2 if head.split else 1
+                nbytes = 2 * planes * total * int(np.prod(head.shape)) * 4
+                if self.in_use + nbytes > self.budget:
+                    if not inflight:
+                        raise RuntimeError("request larger than the HBM budget")
+                    break  # admission: wait until running batches free memory
+                for r in group:
+                    queue.remove(r)
+                sidx = min(free, key=lambda i: per_slot[i])
+                inflight.append(self._launch(group, key, sidx))
+                per_slot[sidx] += 1
+                self.in_use += nbytes
+                self.peak_in_use = max(self.peak_in_use, self.in_use)
+                batches += 1
+                launched = True
+            if not launched and not (pending and pending[0].t_arrival <= time.perf_counter() - t0):
+                time.sleep(20e-6)
+        torch.cuda.synchronize()
+        return self.stats(requests, batches)
+
+    def stats(self, requests, batches):
+        lat = np.array([r.t_done - r.t_arrival for r in requests])
+        span = max(r.t_done for r in requests) - min(r.t_arrival for r in requests)
+        flops = sum(r.flops for r in requests)
+        out = {"requests": len(requests), "batches": batches,
+               "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+               "mean_ms": float(lat.mean() * 1e3), "gflops": flops / span / 1e9, "span_s": span,
+               "peak_hbm_bytes": self.peak_in_use}
+        for split in (False, True):
+            sel = [r for r in requests if r.split == split]
+            if sel:
+                la = np.array([r.t_done - r.t_arrival for r in sel])
+                out["split" if split else "plain"] = {
+                    "requests": len(sel), "p50_ms": float(np.percentile(la, 50) * 1e3),
+                    "p99_ms": float(np.percentile(la, 99) * 1e3),
+                    "gflops": sum(r.flops for r in sel) / span / 1e9}
+        return out
+
+    def close(self):
+        for p in self.plans.values():
+            p.destroy()
+        self.plans.clear()
