@@ -57,8 +57,10 @@ tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int
   else return TCFFT_ERR_INVALID_SIZE;
   // layout contract of the kernel (see SideLayout); a contiguous side with a
   // transform-offset table and I1 == 1 gathers/scatters transform by transform
-  const bool in_gather = in_contig && in.toff && I1 == 1;
-  const bool out_scatter = out_contig && out.toff && I1 == 1;
+  // per-transform ("gather"/"scatter") mode: the transforms of a CTA are not
+  // one contiguous block -- each has its own offset (table) or they sit s1 != L apart
+  const bool in_gather = in_contig && ((in.toff && I1 == 1) || (!in.toff && in.s1 != L));
+  const bool out_scatter = out_contig && ((out.toff && I1 == 1) || (!out.toff && out.s1 != L));
   if ((in_contig && in.s1 != L && !in_gather) || (!in_contig && in.s1 != 1)) return TCFFT_ERR_INVALID_SIZE;
   if ((out_contig && out.s1 != L && !out_scatter) || (!out_contig && out.s1 != 1))
     return TCFFT_ERR_INVALID_SIZE;

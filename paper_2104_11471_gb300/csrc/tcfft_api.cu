@@ -392,12 +392,29 @@ tcfft_status plan_1d(tcfft_plan_s* pl) {
     return add_pass(pl, n, B, kNoLevel, 1, s, s, BUF_IN, BUF_OUT, 0, 0);
   }
   const int lg = ilog2(n);
-  const int64_t N1 = int64_t(1) << ((lg + 1) / 2), N2 = n / N1;
   pl->ws_bytes = (size_t)B * n * 4 * (pl->split ? 2 : 1);
   if (cudaMalloc(&pl->ws, pl->ws_bytes) != cudaSuccess) {
     pl->ws = nullptr;
     return TCFFT_ERR_ALLOC;
   }
+  if (lg >= env_int("TCFFT_THREE_PASS_MIN", 24)) {
+    // n = N1 N2 N3 (M = N2 N3) in three passes of short transforms, so that
+    // every pass keeps small per-CTA tiles with prefetch:
+    //  A: N1-point DFTs of the columns x[M n1 + m], times W_n^{m k1} -> ws
+    //  B: N2-point DFTs of ws[k1 M + N3 n2 + n3], times W_M^{n3 k2}, in place
+    //  C: N3-point DFTs of ws rows (k1, k2) -> X[k1 + N1 k2 + N1 N2 k3]
+    const int l1 = 8, l2 = (lg - 8 + 1) / 2, l3 = lg - 8 - l2;
+    const int64_t N1 = int64_t(1) << l1, N2 = int64_t(1) << l2, N3 = int64_t(1) << l3, M = N2 * N3;
+    Side a{1, n, 0, M};
+    tcfft_status st = add_pass(pl, N1, B * M, M, kNoLevel, a, a, BUF_IN, BUF_WS, 1, lg);
+    if (st != TCFFT_OK) return st;
+    Side b{1, M, n, N3};
+    st = add_pass(pl, N2, B * N1 * N3, N3, N1, b, b, BUF_WS, BUF_WS, 1, l2 + l3);
+    if (st != TCFFT_OK) return st;
+    Side cin{M, N3, n, 1}, cout{1, N1, n, N1 * N2};
+    return add_pass(pl, N3, B * N1 * N2, N1, N2, cin, cout, BUF_WS, BUF_OUT, 0, 0);
+  }
+  const int64_t N1 = int64_t(1) << ((lg + 1) / 2), N2 = n / N1;
   // pass 1: columns n2 of length N1 (stride N2), times W_n^{n2 k1}
   Side c1{1, n, 0, N2};
   tcfft_status st = add_pass(pl, N1, B * N2, N2, kNoLevel, c1, c1, BUF_IN, BUF_WS, 1, lg);

@@ -167,3 +167,12 @@ def test_plans_sharing_a_kernel_with_different_shared_memory():
     check_rows(si.as_complex128(o), oracle.fft_batch(si.as_complex128(h)), PLAIN_TOL, "after second plan")
     big.destroy()
     small.destroy()
+
+
+@pytest.mark.parametrize("log2n,batch", [(24, 1), (22, 2), (21, 3)])
+def test_1d_three_pass_split(log2n, batch, monkeypatch):
+    # the three-pass decomposition (forced down to 2^21 here) against the oracle
+    monkeypatch.setenv("TCFFT_THREE_PASS_MIN", "21")
+    n = 1 << log2n
+    got, x = fft1d_gpu(n, batch, seed=log2n + 40)
+    check_rows(got, oracle.fft_batch(x), PLAIN_TOL, f"three-pass N=2^{log2n}")
