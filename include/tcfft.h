@@ -11,7 +11,8 @@
  *
  * Conventions shared by every call:
  *  - Transform: forward, X[k] = sum_n x[n] exp(-2 pi i n k / N), sign -,
- *    no normalisation (Eq. dft_def, Sec. 2.1).  Output in natural order.
+ *    no normalisation (Eq. dft_def, Sec. 2.1), unless the plan flags ask for
+ *    the inverse and/or 1/N scaling.  Output in natural order.
  *  - Data: interleaved complex FP16 (re, im), 4 bytes per point.  1D
  *    transform b starts at element b*n; 2D data is [batch][nx][ny], row-major
  *    with ny contiguous (the tcfftPlan2D statement in Sec. 3.1).
@@ -65,6 +66,11 @@ typedef enum {
                                   (default $HOME/.cache/tcfft_tune.txt) */
 #define TCFFT_PLAN_GRAPH 2u    /* tcfft_exec replays one instantiated CUDA graph
                                   per (in, out) pair (captured on first use) */
+#define TCFFT_PLAN_INVERSE 4u  /* inverse transform: sign +, X[k] = sum_n x[n]
+                                  exp(+2 pi i n k / N), unnormalised */
+#define TCFFT_PLAN_SCALE 8u    /* multiply the results by 1/N (N = points of one
+                                  transform); with TCFFT_PLAN_INVERSE the exact
+                                  inverse of the forward transform */
 
 /* Plan a batch of `batch` 1D transforms of length n (the paper's
  * tcfftPlan1D(plan, nx, batch), Sec. 3.1).  Allocates device twiddle tables

@@ -23,6 +23,8 @@ TCFFT_FP16 = 0
 TCFFT_FP16_SPLIT = 1
 TCFFT_PLAN_AUTOTUNE = 1
 TCFFT_PLAN_GRAPH = 2
+TCFFT_PLAN_INVERSE = 4
+TCFFT_PLAN_SCALE = 8
 
 STATUS = {
     0: "TCFFT_OK", 1: "TCFFT_ERR_INVALID_SIZE", 2: "TCFFT_ERR_INVALID_VALUE",

@@ -330,6 +330,16 @@ __device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, con
         lv[n0][4] = d.x; lv[n0][5] = d.y; lv[n0][6] = d.z; lv[n0][7] = d.w;
       }
     }
+    if (p.conj_in) {
+      // inverse transform: conj(x) on the way in (sign bit of each imaginary half)
+#pragma unroll
+      for (int n0 = 0; n0 < RX; ++n0)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          hv[n0][i] ^= 0x80000000u;
+          if constexpr (K::SPLIT) lv[n0][i] ^= 0x80000000u;
+        }
+    }
     if constexpr (RX > 1) {
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
@@ -344,6 +354,10 @@ __device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, con
           }
         }
         small_dft<RX>(v);
+        if (p.prescale != 1.0f) {
+#pragma unroll
+          for (int k0 = 0; k0 < RX; ++k0) v[k0] = make_float2(v[k0].x * p.prescale, v[k0].y * p.prescale);
+        }
         const uint32_t npi = K::IN_C ? (uint32_t)(np + i) : (uint32_t)np;
 #pragma unroll
         for (int k0 = 0; k0 < RX; ++k0) {
@@ -710,6 +724,11 @@ __global__ void __launch_bounds__(kThreads, SPLIT ? 1 : 2)
                 d2 = dn;
               }
             }
+          }
+          if (p.conj_out) {
+            // inverse transform: conj() of the result
+#pragma unroll
+            for (int i = 0; i < 8; ++i) Y[i] = make_float2(-Y[i].x, -Y[i].y);
           }
           if constexpr (K::DIRECT_OUT) {
             // lanes hold consecutive output indices: store straight to global

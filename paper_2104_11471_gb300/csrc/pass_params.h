@@ -58,6 +58,9 @@ struct PassParams {
   int otw_log2S;
   const float* otw_lo;
   const float* otw_hi;
+  int conj_in;            // negate imaginary parts on load (first pass of an inverse)
+  int conj_out;           // negate imaginary parts of the results (last pass of an inverse)
+  float prescale;         // factor on the leading radix-R step (1/R when the pass is scaled)
   int in_gather;          // contiguous input, one offset per transform (see SideLayout)
   int out_scatter;        // contiguous output, one offset per transform
   int async_load;         // 1: prefetch the next chunk with cp.async into a raw buffer

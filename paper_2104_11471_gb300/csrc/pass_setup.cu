@@ -120,6 +120,7 @@ tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int
   p.log2I2 = ilog2(I2);
   p.in_l = SideLayout{in.s1, in.s2, in.s3, (uint32_t)in.es, in.toff};
   p.out_l = SideLayout{out.s1, out.s2, out.s3, (uint32_t)out.es, out.toff};
+  p.prescale = 1.0f;
   p.in_gather = in_gather;
   p.out_scatter = out_scatter;
   p.nchunks = (T + C - 1) / C;

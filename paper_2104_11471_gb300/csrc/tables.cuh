@@ -65,13 +65,14 @@ static __global__ void stage_twiddle_kernel(float4* out, int log2N, int rows) {
 //   B[k][n]: k < 16 -> Re of input k, k >= 16 -> Im of input k-16;
 //            n < 16 -> Re of output n, n >= 16 -> Im of output n-16;
 //   [[Re M, Im M], [-Im M, Re M]].
+// Scaled plans (1/N spread over the stages) use M / 16.
 // Image k0 (k0 < RX) holds M[m][l] = W_16^{l m} W_{16 RX}^{k0 m}
 // = W_{16 RX}^{m (RX l + k0)}: the DFT matrix F_16 with the leading-radix
 // twiddle factor of input n_1 = m folded in (image 0 is plain F_16).
 // Stored K-major without swizzle: core matrices of 8 (n) x 8 (k) halves,
 // K-groups 128 B apart, N-groups 512 B apart.  Images 0..7 hold the FP16
 // values, images 8..15 the low parts fp16((v - hi) * 2^11) for split precision.
-static __global__ void dft_b_kernel(__half* img, int RX) {
+static __global__ void dft_b_kernel(__half* img, int RX, double scale = 1.0) {
   const int k0 = blockIdx.x;    // one block per image
   const int idx = threadIdx.x;  // 1024 threads: one per (k, n)
   const int k = idx >> 5, n = idx & 31;
@@ -82,6 +83,7 @@ static __global__ void dft_b_kernel(__half* img, int RX) {
   double v;
   if (k < 16) v = (n < 16) ? c : s;
   else v = (n < 16) ? -s : c;
+  v *= scale;  // 1/16 for scaled plans: exact in FP16
   const int off = k0 * 1024 + (n >> 3) * 256 + (k >> 3) * 64 + (n & 7) * 8 + (k & 7);  // halves
   const __half h = __double2half(v);
   img[off] = h;

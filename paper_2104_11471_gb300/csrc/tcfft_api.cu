@@ -84,7 +84,7 @@ struct tcfft_plan_s {
   int64_t points = 0;  // total complex points per plane
   std::vector<Pass> passes;
   std::map<int, TwTable> tables;
-  std::map<int, __half*> dft_b;  // by leading radix RX
+  std::map<int, __half*> dft_b;  // by 2 * leading radix RX + scaled
   int* d_status = nullptr;
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -92,6 +92,8 @@ struct tcfft_plan_s {
   void* h_out_dev = nullptr;
   size_t table_bytes = 0;
   bool autotune = false;              // time candidate geometries at plan time
+  bool inverse = false;               // sign + (TCFFT_PLAN_INVERSE)
+  bool normalise = false;             // results times 1/N (TCFFT_PLAN_SCALE)
   bool use_graph = false;             // exec replays a captured CUDA graph
   std::vector<int64_t*> toff_tables;  // device transform-offset tables (ragged)
   std::vector<GraphEntry> graphs;     // instantiated graphs by (in, out)
@@ -118,8 +120,9 @@ struct tcfft_plan_s {
 
   std::map<int, float*> stage_tables;  // by log2 of the pass length
 
-  tcfft_status b_images(int RX, const __half** out) {
-    auto it = dft_b.find(RX);
+  tcfft_status b_images(int RX, const __half** out, bool scaled = false) {
+    const int key = RX * 2 + (scaled ? 1 : 0);
+    auto it = dft_b.find(key);
     if (it != dft_b.end()) {
       *out = it->second;
       return TCFFT_OK;
@@ -128,12 +131,12 @@ struct tcfft_plan_s {
     if (cudaMalloc(&b, 16 * kBImageBytes) != cudaSuccess) return TCFFT_ERR_ALLOC;
     cudaMemset(b, 0, 16 * kBImageBytes);
     table_bytes += 16 * kBImageBytes;
-    dft_b_kernel<<<RX, 1024>>>(b, RX);
+    dft_b_kernel<<<RX, 1024>>>(b, RX, scaled ? 1.0 / 16.0 : 1.0);
     if (cudaGetLastError() != cudaSuccess) {
       cudaFree(b);
       return TCFFT_ERR_LAUNCH;
     }
-    dft_b[RX] = b;
+    dft_b[key] = b;
     *out = b;
     return TCFFT_OK;
   }
@@ -234,7 +237,7 @@ tcfft_status bind_tables(tcfft_plan_s* pl, Pass& ps, int log2L, int otw_level, i
   if (st != TCFFT_OK) return st;
   p.stw = reinterpret_cast<const float4*>(stw);
   const __half* bimg = nullptr;
-  st = pl->b_images(1 << (log2L % 4), &bimg);
+  st = pl->b_images(1 << (log2L % 4), &bimg, pl->normalise);
   if (st != TCFFT_OK) return st;
   p.dft_b = reinterpret_cast<const uint16_t*>(bimg);
   p.otw_level = otw_level;
@@ -521,11 +524,38 @@ tcfft_status plan_many(tcfft_plan_s* pl, int64_t count, const int64_t* n0, const
   return TCFFT_OK;
 }
 
-constexpr unsigned kPlanFlags = TCFFT_PLAN_AUTOTUNE | TCFFT_PLAN_GRAPH;
+constexpr unsigned kPlanFlags = TCFFT_PLAN_AUTOTUNE | TCFFT_PLAN_GRAPH | TCFFT_PLAN_INVERSE | TCFFT_PLAN_SCALE;
 
 void apply_flags(tcfft_plan_s* pl, unsigned flags) {
   pl->autotune = (flags & TCFFT_PLAN_AUTOTUNE) || env_int("TCFFT_AUTOTUNE", 0);
   pl->use_graph = (flags & TCFFT_PLAN_GRAPH) != 0;
+  pl->inverse = (flags & TCFFT_PLAN_INVERSE) != 0;
+  pl->normalise = (flags & TCFFT_PLAN_SCALE) != 0;
+}
+
+// Direction and scaling: the inverse DFT is conj(DFT(conj(x))), so the first
+// pass of each transform conjugates its input and the last conjugates (and,
+// with TCFFT_PLAN_SCALE, scales by 1/N) its output.  In a ragged plan the
+// passes of each group are consecutive; the scale is per group.
+void apply_direction(tcfft_plan_s* pl) {
+  if (!pl->inverse && !pl->normalise) return;
+  size_t i = 0;
+  while (i < pl->passes.size()) {
+    size_t j = i;
+    while (j + 1 < pl->passes.size() && pl->passes[j + 1].group == pl->passes[i].group) ++j;
+    int64_t n = 1;  // transform size of the group: product of its pass lengths
+    for (size_t k = i; k <= j; ++k) n *= int64_t(1) << pl->passes[k].p.log2N;
+    if (pl->dims == 2) n = pl->nx * pl->ny;
+    pl->passes[i].p.conj_in = pl->inverse ? 1 : 0;
+    pl->passes[j].p.conj_out = pl->inverse ? 1 : 0;
+    // 1/N is spread over the transform: every radix-16 stage uses F_16 / 16
+    // (scaled DFT-matrix images, bound in bind_tables) and every leading
+    // radix-R step scales by 1/R, so intermediates keep the input's magnitude
+    if (pl->normalise)
+      for (size_t k = i; k <= j; ++k) pl->passes[k].p.prescale = 1.0f / (float)(1 << (pl->passes[k].p.log2N % 4));
+    (void)n;
+    i = j + 1;
+  }
 }
 
 tcfft_status check_device() {
@@ -663,6 +693,7 @@ tcfft_status tcfft_plan_1d_ex(tcfft_plan* plan, int64_t n, int64_t batch, tcfft_
   apply_flags(pl, flags);
   st = common_init(pl);
   if (st == TCFFT_OK) st = plan_1d(pl);
+  if (st == TCFFT_OK) apply_direction(pl);
   return finish(pl, st, plan);
 }
 
@@ -693,6 +724,7 @@ tcfft_status tcfft_plan_2d_ex(tcfft_plan* plan, int64_t nx, int64_t ny, int64_t 
   apply_flags(pl, flags);
   st = common_init(pl);
   if (st == TCFFT_OK) st = plan_2d(pl);
+  if (st == TCFFT_OK) apply_direction(pl);
   return finish(pl, st, plan);
 }
 
@@ -726,6 +758,7 @@ tcfft_status tcfft_plan_many(tcfft_plan* plan, int64_t count, const int64_t* n0,
   apply_flags(pl, flags);
   st = common_init(pl);
   if (st == TCFFT_OK) st = plan_many(pl, count, n0, n1);
+  if (st == TCFFT_OK) apply_direction(pl);
   return finish(pl, st, plan);
 }
 
