@@ -72,6 +72,12 @@ struct PassCfg {
   // consecutive output indices (two radix-16 stages, no leading radix,
   // contiguous output)
   static constexpr bool DIRECT_OUT = OUT_C && S == 2 && RX == 1;
+  // CTAs per SM the register budget is sized for (the kernel is latency-bound:
+  // more resident warps hide the TMEM, barrier and memory waits).  Plain
+  // lengths fit 80 registers (3 CTAs of 256 threads) without spills except
+  // those with a radix-8 leading step or a single radix-16 stage after a
+  // radix 2/4 step, which keep 2.
+  static constexpr int MINB = SPLIT ? 1 : ((LOG2N_ % 4 == 3 || (LOG2N_ > 4 && LOG2N_ < 8)) ? 2 : 3);
   static_assert(S >= 1 && S <= 3, "pass length out of range");
 };
 
@@ -434,7 +440,7 @@ __device__ __forceinline__ RowChunks row_chunks(uint32_t m0, uint32_t k) {
 // shared memory (bulk copy or cp.async) while the current chunk runs its
 // MMA stages, epilogues and stores.
 template <int LOG2N, int MODE, bool SPLIT>
-__global__ void __launch_bounds__(kThreads, SPLIT ? 1 : 2)
+__global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
     pass_kernel(const __grid_constant__ PassParams p) {
   using K = PassCfg<LOG2N, MODE, SPLIT>;
   extern __shared__ uint8_t smem_raw[];
