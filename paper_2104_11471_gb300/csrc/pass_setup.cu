@@ -131,15 +131,11 @@ tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int
   const size_t base = 1024 + (size_t)planes * p.tiles * kTileBytes + (size_t)planes * nb * kBImageBytes +
                       64;  // + 2 mbarriers, TMEM slot
   const size_t raw = (size_t)planes * P * 4;
-  p.async_load = (base + raw <= 227 * 1024) ? 1 : 0;
-  if (env_int("TCFFT_SYNC_LOAD", 0)) p.async_load = 0;  // debugging override
-  size_t smem = base + (p.async_load ? raw : 0);
   const int ctas_tmem = 512 / cols;
   const size_t sm_total = 228 * 1024;
   const size_t per_cta_max = sm_total / ctas_tmem - 1024;
-  if (smem < per_cta_max) smem = std::min<size_t>(per_cta_max, 227 * 1024);
-  if (smem > 227 * 1024) return TCFFT_ERR_INVALID_SIZE;
-  ps.smem = smem;
+  // padded so that shared memory, not TMEM allocation, limits CTAs per SM
+  auto padded = [&](size_t sm) { return sm < per_cta_max ? std::min<size_t>(per_cta_max, 227 * 1024) : sm; };
   // the attribute is a per-kernel upper bound shared by every pass (and plan)
   // that launches this kernel: always the largest, never the pass's own size
   if (cudaFuncSetAttribute(ps.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
@@ -159,11 +155,24 @@ tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int
   if (cudaFuncGetAttributes(&fa0, ps.fn) != cudaSuccess) return TCFFT_ERR_CUDA;
   const int warp_regs = ((fa0.numRegs * 32 + 255) / 256) * 256;
   const int by_regs = regs_sm / (warp_regs * (kThreads / 32));
-  const int by_smem = smem_sm / (int)(smem + fa0.sharedSizeBytes + 1024);
   const int by_thr = thr_sm / kThreads;
-  int occ = std::min(by_regs, std::min(by_smem, by_thr));
+  auto occupancy = [&](size_t sm) {
+    const int by_smem = smem_sm / (int)(sm + fa0.sharedSizeBytes + 1024);
+    return std::min(ctas_tmem, std::min(by_regs, std::min(by_smem, by_thr)));
+  };
+  // prefetch the next chunk into a raw buffer when it fits, unless the
+  // buffer costs resident CTAs: the pass is latency-bound, and a second CTA
+  // per SM hides more than one chunk of prefetch (measured at 16384 points
+  // per CTA: 0.83 ms synchronous at 2 CTAs/SM vs 1.11 ms prefetched at 1)
+  const size_t sm_async = padded(base + raw), sm_sync = padded(base);
+  const bool async_fits = base + raw <= 227 * 1024;
+  p.async_load = (async_fits && occupancy(sm_async) >= occupancy(sm_sync)) ? 1 : 0;
+  if (env_int("TCFFT_SYNC_LOAD", 0)) p.async_load = 0;  // debugging override
+  const size_t smem = p.async_load ? sm_async : sm_sync;
+  if (smem > 227 * 1024) return TCFFT_ERR_INVALID_SIZE;
+  ps.smem = smem;
+  int occ = occupancy(smem);
   if (occ < 1) return TCFFT_ERR_INVALID_SIZE;
-  occ = std::min(occ, ctas_tmem);
   const int occ_env = env_int("TCFFT_CTAS_PER_SM", 0);  // tuning override
   if (occ_env > 0) occ = std::min(occ, occ_env);
   ps.grid = dim3((unsigned)std::min<int64_t>(p.nchunks, (int64_t)occ * sms));
