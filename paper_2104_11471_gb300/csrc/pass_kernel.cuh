@@ -256,7 +256,7 @@ __device__ __forceinline__ void issue_raw_copy(const PassParams& p, uint32_t raw
     for (int pl = 0; pl < K::PLANES; ++pl) {
       const uint32_t* g = gin + (pl ? p.in_plane : 0);
       const uint32_t dst0 = raw_s + pl * (P * 4u);
-      for (uint32_t q = threadIdx.x; q < nq; q += kThreads) {
+      for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x) {
         const uint32_t off = (q >> cq) * p.in_l.es + ((q & ((1u << cq) - 1u)) << 2);
         cp_async16(dst0 + (q << 4), g + off, 16);
       }
@@ -283,7 +283,7 @@ __device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, con
   // items: 8 points (contiguous: of one transform; strided: of 8 transforms)
   constexpr int BLOG = K::LOG2L - 3;
   const int items = K::IN_C ? (C << BLOG) : (K::L << (log2C - 3));
-  for (int it = threadIdx.x; it < items; it += kThreads) {
+  for (int it = threadIdx.x; it < items; it += (int)blockDim.x) {
     int c, np;  // transform (first of 8 when strided), point n' in [0, L)
     uint32_t off0, step;
     bool valid = true;
@@ -461,6 +461,7 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
   const int warp = tid >> 5, lane = tid & 31;
   const int quarter = warp & 3;  // TMEM lane quarter of this warp
   const int half = warp >> 2;    // which tiles this warp takes in the epilogue
+  const int halves = (int)(blockDim.x >> 7);  // warps per TMEM lane quarter
 
   // DFT matrix images -> shared memory: hi images k0 = 0..NB-1, then (split)
   // the lo images; the global table holds 8 hi then 8 lo images.
@@ -468,7 +469,7 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
     const uint4* src = reinterpret_cast<const uint4*>(p.dft_b);
     uint4* dst = reinterpret_cast<uint4*>(Bs);
     constexpr int per = kBImageBytes / 16;
-    for (int i = tid; i < K::PLANES * NB * per; i += kThreads) {
+    for (int i = tid; i < K::PLANES * NB * per; i += (int)blockDim.x) {
       const int plane = i / (NB * per), r = i - plane * (NB * per);
       dst[i] = __ldg(src + plane * 8 * per + r);
     }
@@ -584,7 +585,7 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
       tc_fence_after_sync();
 
       const bool last = (j == K::S);
-      for (int t = half; t < tiles; t += 2) {
+      for (int t = half; t < tiles; t += halves) {
         const uint32_t row = (uint32_t)t * 128u + 32u * quarter + lane;
         // X[i] = (Re out 2i, Re out 2i+1), Y[i] = (Im out 2i, Im out 2i+1)
         float2 X[8], Y[8];
@@ -784,7 +785,7 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
       const uint32_t nch = P >> 2;
       if constexpr (K::OUT_C) {
         const uint32_t vchunks = ((uint32_t)nvalid << LOG2N) >> 2;
-        for (uint32_t q = tid; q < vchunks; q += kThreads) {
+        for (uint32_t q = tid; q < vchunks; q += blockDim.x) {
           const uint32_t c = (q << 2) >> LOG2N;
           const uint32_t ko = (q << 2) & (K::N - 1);
           const uint32_t pq = q ^ stg_key<K>(c, ko, log2C);
@@ -796,7 +797,7 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
       } else {
         const int cq = log2C - 2;  // log2 of the chunks per output element index
         const uint32_t es = p.out_l.es;
-        for (uint32_t q = tid; q < nch; q += kThreads) {
+        for (uint32_t q = tid; q < nch; q += blockDim.x) {
           const uint32_t ko = q >> cq;
           const uint32_t cc = (q & ((1u << cq) - 1u)) << 2;
           const uint32_t off = ko * es + cc;

@@ -42,8 +42,11 @@ const void* pass_fn(int log2N, int mode, bool split) {
   }
 }
 
-tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int64_t I2, Side in,
-                           Side out, bool split, int64_t target_points) {
+namespace {
+// One candidate geometry: `threads` per CTA (256 or 128), prefetching the next
+// chunk into a raw buffer (async = 1) or loading synchronously (async = 0).
+tcfft_status geometry_try(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int64_t I2, Side in, Side out,
+                          bool split, int64_t target_points, int threads, int async) {
 
   std::memset(&ps.p, 0, sizeof(ps.p));
   PassParams& p = ps.p;
@@ -68,9 +71,12 @@ tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int
   ps.fn = pass_fn(log2L, mode, split);
   if (!ps.fn) return TCFFT_ERR_INVALID_SIZE;
   const int64_t cap = split ? kCapSplit : kCapPlain;
+  // the default chunk sizes scale with the threads per CTA
+  ps.threads = threads;
+  const int64_t tscale = ps.threads / 128;  // 1 or 2
   int64_t C;
   if (mode == kModeContig) {
-    int64_t target = split ? 4096 : 8192;
+    int64_t target = (split ? 2048 : 4096) * tscale;
     const int tgt_env = env_int("TCFFT_POINTS_PER_CTA", 0);  // tuning override
     if (tgt_env >= 2048 && is_pow2(tgt_env)) target = tgt_env;
     if (target_points >= 2048 && is_pow2(target_points)) target = target_points;
@@ -79,7 +85,7 @@ tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int
       while (C > 1 && I1 % C != 0) C /= 2;
   } else {
     // strided side: C adjacent transforms per element index, C | I1, C >= 8
-    int64_t soft = split ? 4096 : 8192;
+    int64_t soft = (split ? 2048 : 4096) * tscale;
     const int soft_env = env_int("TCFFT_STRIDED_POINTS", 0);  // tuning override
     if (soft_env >= 1024 && is_pow2(soft_env)) soft = soft_env;
     if (target_points >= 1024 && is_pow2(target_points)) soft = target_points;
@@ -154,21 +160,15 @@ tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int
   cudaFuncAttributes fa0;
   if (cudaFuncGetAttributes(&fa0, ps.fn) != cudaSuccess) return TCFFT_ERR_CUDA;
   const int warp_regs = ((fa0.numRegs * 32 + 255) / 256) * 256;
-  const int by_regs = regs_sm / (warp_regs * (kThreads / 32));
-  const int by_thr = thr_sm / kThreads;
+  const int by_regs = regs_sm / (warp_regs * (ps.threads / 32));
+  const int by_thr = thr_sm / ps.threads;
   auto occupancy = [&](size_t sm) {
     const int by_smem = smem_sm / (int)(sm + fa0.sharedSizeBytes + 1024);
     return std::min(ctas_tmem, std::min(by_regs, std::min(by_smem, by_thr)));
   };
-  // prefetch the next chunk into a raw buffer when it fits, unless the
-  // buffer costs resident CTAs: the pass is latency-bound, and a second CTA
-  // per SM hides more than one chunk of prefetch (measured at 16384 points
-  // per CTA: 0.83 ms synchronous at 2 CTAs/SM vs 1.11 ms prefetched at 1)
-  const size_t sm_async = padded(base + raw), sm_sync = padded(base);
-  const bool async_fits = base + raw <= 227 * 1024;
-  p.async_load = (async_fits && occupancy(sm_async) >= occupancy(sm_sync)) ? 1 : 0;
-  if (env_int("TCFFT_SYNC_LOAD", 0)) p.async_load = 0;  // debugging override
-  const size_t smem = p.async_load ? sm_async : sm_sync;
+  if (async && base + raw > 227 * 1024) return TCFFT_ERR_INVALID_SIZE;
+  p.async_load = async;
+  const size_t smem = padded(async ? base + raw : base);
   if (smem > 227 * 1024) return TCFFT_ERR_INVALID_SIZE;
   ps.smem = smem;
   int occ = occupancy(smem);
@@ -177,8 +177,45 @@ tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int
   if (occ_env > 0) occ = std::min(occ, occ_env);
   ps.grid = dim3((unsigned)std::min<int64_t>(p.nchunks, (int64_t)occ * sms));
   ps.occ = occ;
-  cudaFuncAttributes fa;
-  ps.regs = (cudaFuncGetAttributes(&fa, ps.fn) == cudaSuccess) ? fa.numRegs : -1;
+  ps.regs = fa0.numRegs;
+  return TCFFT_OK;
+}
+}  // namespace
+
+tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int64_t I2, Side in,
+                           Side out, bool split, int64_t target_points) {
+  // The pass is latency-bound (TMEM loads, MMA completion, barriers, memory):
+  // pick the candidate with the most resident warps per SM.  A synchronous
+  // load exposes its latency and counts 0.7 of a prefetching one; at equal
+  // warps more, smaller CTAs win (fewer warps wait at each barrier).
+  // Measured at 2^28 points: N = 256 at 6 x 128 threads 0.38 ms vs 3 x 256
+  // 0.43 ms; N = 16384 at 2 x 256 synchronous 0.82 ms vs 1 x 256 prefetching
+  // 1.11 ms; 2^18 (length-512 passes) 3 x 256 prefetching 1.25 ms vs 6 x 128
+  // synchronous 1.51 ms.
+  const int thr_env = env_int("TCFFT_THREADS", 0);   // tuning override
+  const int sync_env = env_int("TCFFT_SYNC_LOAD", 0);  // debugging override
+  PassLaunch best;
+  double best_score = -1.0;
+  tcfft_status last = TCFFT_ERR_INVALID_SIZE;
+  for (int thr : {256, 128}) {
+    if ((thr_env == 128 || thr_env == 256) && thr != thr_env) continue;
+    for (int as : {1, 0}) {
+      if (as && sync_env) continue;
+      PassLaunch c = ps;
+      const tcfft_status st = geometry_try(c, L, T, I1, I2, in, out, split, target_points, thr, as);
+      if (st != TCFFT_OK) {
+        last = st;
+        continue;
+      }
+      const double score = c.occ * (thr / 32) * (as ? 1.0 : 0.7) + c.occ * 1e-3;
+      if (score > best_score) {
+        best = c;
+        best_score = score;
+      }
+    }
+  }
+  if (best_score < 0) return last;
+  ps = best;
   return TCFFT_OK;
 }
 

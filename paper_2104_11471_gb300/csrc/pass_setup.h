@@ -24,6 +24,7 @@ struct PassLaunch {
   size_t smem = 0;
   int occ = 0;   // CTAs per SM the grid was sized for
   int regs = 0;  // registers per thread of the kernel
+  int threads = kThreads;  // threads per CTA (a multiple of 128: one warp per TMEM lane quarter)
 };
 
 int ilog2(int64_t v);

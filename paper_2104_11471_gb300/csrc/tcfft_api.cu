@@ -341,7 +341,7 @@ tcfft_status tune_pass(tcfft_plan_s* pl, Pass& ps, int64_t L, int64_t T, int64_t
       bool okc = true;
       for (int rep = 0; rep < 4 && okc; ++rep) {  // first run is a warm-up
         cudaEventRecord(e0);
-        okc = cudaLaunchKernel(c.fn, c.grid, dim3(kThreads), args, c.smem, 0) == cudaSuccess;
+        okc = cudaLaunchKernel(c.fn, c.grid, dim3(c.threads), args, c.smem, 0) == cudaSuccess;
         cudaEventRecord(e1);
         cudaEventSynchronize(e1);
         float t = 0.0f;
@@ -617,7 +617,7 @@ tcfft_status exec_graph(tcfft_plan_s* plan, const void* in, void* out, cudaStrea
     cudaKernelNodeParams kp = {};
     kp.func = const_cast<void*>(ps.fn);
     kp.gridDim = ps.grid;
-    kp.blockDim = dim3(kThreads);
+    kp.blockDim = dim3(ps.threads);
     kp.sharedMemBytes = (unsigned)ps.smem;
     kp.kernelParams = args;
     cudaGraphNode_t node;
@@ -775,7 +775,7 @@ tcfft_status tcfft_exec(tcfft_plan plan, const void* in, void* out, void* stream
   for (const Pass& ps : plan->passes) {
     PassParams p = bound_params(plan, ps, in, out);
     void* args[1] = {&p};
-    cudaError_t e = cudaLaunchKernel(ps.fn, ps.grid, dim3(kThreads), args, ps.smem, s);
+    cudaError_t e = cudaLaunchKernel(ps.fn, ps.grid, dim3(ps.threads), args, ps.smem, s);
     if (e != cudaSuccess) {
       if (env_int("TCFFT_DEBUG", 0))
         std::fprintf(stderr, "tcfft_exec: launch of pass (log2n %d, grid %u, smem %zu) failed: %s\n",
@@ -806,7 +806,7 @@ tcfft_status tcfft_exec_batch(tcfft_plan plan, const void* in, void* out, int64_
     if (ps.dst != BUF_WS) p.out_plane = per * batch;
     const dim3 grid((unsigned)std::min<int64_t>(p.nchunks, (int64_t)ps.grid.x));
     void* args[1] = {&p};
-    if (cudaLaunchKernel(ps.fn, grid, dim3(kThreads), args, ps.smem, s) != cudaSuccess) return TCFFT_ERR_LAUNCH;
+    if (cudaLaunchKernel(ps.fn, grid, dim3(ps.threads), args, ps.smem, s) != cudaSuccess) return TCFFT_ERR_LAUNCH;
   }
   return TCFFT_OK;
 }
