@@ -443,7 +443,7 @@ template <int LOG2N, int MODE, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
     pass_kernel(const __grid_constant__ PassParams p) {
   using K = PassCfg<LOG2N, MODE, SPLIT>;
-  extern __shared__ uint8_t smem_raw[];
+  extern __shared__ __align__(16) uint8_t smem_raw[];
   uint8_t* A = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                           ~uintptr_t(1023));
   const int tiles = p.tiles;
@@ -453,7 +453,11 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
   uint8_t* RAW = A + K::PLANES * tiles * kTileBytes;
   constexpr int NB = K::FOLD ? K::RX : 1;  // DFT matrix images per plane
   uint8_t* Bs = RAW + (p.async_load ? K::PLANES * P * 4u : 0u);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(Bs + K::PLANES * NB * kBImageBytes);
+  // barrier words and the TMEM slot (64 bytes) sit in the 1 KB alignment
+  // slack below A when it has room, else after the B images; the host
+  // reserves 1008 bytes of slack (the base is 16-byte aligned)
+  const uint32_t slack = (uint32_t)(A - smem_raw);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(slack >= 64 ? A - 64 : Bs + K::PLANES * NB * kBImageBytes);
   uint64_t* lbar = mbar + 1;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
 

@@ -131,11 +131,13 @@ tcfft_status geometry_try(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int6
   p.out_scatter = out_scatter;
   p.nchunks = (T + C - 1) / C;
   // shared memory: A tiles (x planes), raw prefetch buffer (x planes, when it
-  // fits), B image(s), barrier words, 1 KB alignment slack; padded so that
-  // shared memory, not TMEM allocation, limits CTAs per SM.
+  // fits), B image(s) and up to 1008 bytes of slack that aligns A to 1 KB
+  // (the dynamic base is 16-byte aligned) and holds the two mbarriers and the
+  // TMEM slot when it has 64 bytes to spare (else they follow the B images,
+  // within the same 1008 bytes); padded so that shared memory, not TMEM
+  // allocation, limits CTAs per SM.
   const size_t nb = fold ? (size_t)RX : 1;  // DFT matrix images per plane
-  const size_t base = 1024 + (size_t)planes * p.tiles * kTileBytes + (size_t)planes * nb * kBImageBytes +
-                      64;  // + 2 mbarriers, TMEM slot
+  const size_t base = 1008 + (size_t)planes * p.tiles * kTileBytes + (size_t)planes * nb * kBImageBytes;
   const size_t raw = (size_t)planes * P * 4;
   const int ctas_tmem = 512 / cols;
   const size_t sm_total = 228 * 1024;
