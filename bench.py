@@ -607,6 +607,39 @@ def run_gpu(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def write_traffic(args):
+    """Per-step DRAM traffic from an ncu CSV log (one warm-up and one timed
+    step, pass_kernel launches only), scaled from the captured points per exec
+    to the benchmark's; stored with the kernel-source hash it belongs to."""
+    import csv
+    by_id = {}
+    with open(args.write_traffic) as f:
+        rows = [r for r in csv.reader(line for line in f if line.startswith('"'))]
+    hdr = rows[0]
+    ki, mi, vi, ii = (hdr.index(k) for k in ("Kernel Name", "Metric Name", "Metric Value", "ID"))
+    for r in rows[1:]:
+        if "pass_kernel" not in r[ki] or r[mi] not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            continue
+        by_id[int(r[ii])] = by_id.get(int(r[ii]), 0.0) + float(r[vi].replace(",", ""))
+    ids = sorted(by_id)
+    if not ids or len(ids) % 2:
+        raise SystemExit(f"expected the launches of two steps, found {len(ids)}")
+    step = ids[len(ids) // 2:]
+    measured = sum(by_id[i] for i in step)
+    scale = 2 ** (28 - args.log2_points)
+    out = {"kernel_hash": kernel_hash(), "traffic_bytes_per_step": int(measured * scale),
+           "measured_bytes_per_step_at_2^%d_points" % args.log2_points: int(measured), "scale": scale,
+           "launches_per_step": len(step),
+           "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum over the pass_kernel launches of the "
+                   "timed step, scaled to 2^28 points per exec (every launch reads and writes its data "
+                   "once, so traffic grows in proportion)"}
+    path = os.path.join(ROOT, "profiles", f"traffic_{args.workload}.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+    print(json.dumps(out))
+
+
 def kernel_hash() -> str:
     """Hash of the kernel sources, so stored ncu traffic is dropped once they change."""
     import hashlib
@@ -637,7 +670,14 @@ def main():
                     help="sweep1d: the 1D sweep (default); 2d: batched 2D plain and split; "
                          "ragged: mixed sizes in one graph launch")
     ap.add_argument("--no-autotune", action="store_true", help="ragged: skip plan-time autotuning")
+    ap.add_argument("--write-traffic", default="", metavar="CSV",
+                    help="write profiles/traffic_<workload>.json from an ncu --csv log of "
+                         "dram__bytes_read.sum and dram__bytes_write.sum over pass_kernel launches of "
+                         "this command run with --steps 1 --warmup 1 (the second step is kept)")
     args = ap.parse_args()
+    if args.write_traffic:
+        write_traffic(args)
+        return
     global POINTS
     POINTS = 1 << args.log2_points
     world, rank, local = dist_setup()
