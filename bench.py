@@ -463,6 +463,73 @@ def run_serve(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_latency(args, world, rank, local):
+    """Small-batch latency: one large transform (or a few) at a time, inputs
+    resident; per configuration the median over repeated execs of the device
+    time (CUDA events around tcfft_exec) and of the host time (tcfft_exec plus
+    a stream synchronize), with per-pass launches and with one graph launch."""
+    import numpy as np
+    import torch
+    import paper_2104_11471_gb300 as tc
+    tc.build()
+    torch.cuda.set_device(local)
+    reps = max(50, args.steps)
+    configs = [(16, 1), (16, 4), (20, 1), (20, 4), (24, 1), (24, 4)]
+    if args.sizes:
+        keep = {int(v) for v in args.sizes.split(",")}
+        configs = [c for c in configs if c[0] in keep]
+    s = torch.cuda.current_stream()
+    out, tot_flops, tot_s = [], 0.0, 0.0
+    clk = ClockSampler(local)
+    barrier(world)
+    clk.start()
+    launches = 0
+    for lg, batch in configs:
+        n = 1 << lg
+        x = torch.from_numpy(_half_draw(2 * n * batch, 3000 + lg).view(np.uint16)).to(f"cuda:{local}")
+        y = torch.empty_like(x)
+        row = {"n": n, "batch": batch}
+        for name, flags in (("launches", 0), ("graph", tc.TCFFT_PLAN_GRAPH)):
+            plan = tc.Plan.plan_1d(n, batch, tc.TCFFT_FP16, flags)
+            for _ in range(5):
+                plan.exec(x, y, s)
+            torch.cuda.synchronize()
+            dev, host = [], []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                t0 = time.perf_counter()
+                e0.record(s)
+                plan.exec(x, y, s)
+                e1.record(s)
+                s.synchronize()
+                host.append(time.perf_counter() - t0)
+                dev.append(e0.elapsed_time(e1) * 1e-3)
+            launches += reps * plan.num_launches
+            row[name] = {"device_us": round(float(np.median(dev)) * 1e6, 2),
+                         "host_us": round(float(np.median(host)) * 1e6, 2),
+                         "passes": plan.num_launches}
+            if name == "graph":
+                tot_flops += flops_1d(n, batch)
+                tot_s += float(np.median(dev))
+            plan.destroy()
+        out.append(row)
+    clocks = clk.stop()
+    value = world * tot_flops / tot_s / 1e9
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": reps,
+        "warmup": 5, "ms_per_step": tot_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+        "config": {"workload": "latency: 1D N = 2^16, 2^20, 2^24 at batch 1 and 4, one exec at a time, "
+                               "inputs resident; value = flops over the sum of median graph-launch device times",
+                   "parallelism": f"replicas x{world}"},
+        "latency": out,
+        "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_gpu(args, world, rank, local):
     import numpy as np
     import torch
@@ -666,9 +733,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the sampled oracle check of the outputs")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
-    ap.add_argument("--workload", default="sweep1d", choices=["sweep1d", "2d", "ragged", "serve"],
+    ap.add_argument("--workload", default="sweep1d", choices=["sweep1d", "2d", "ragged", "serve", "latency"],
                     help="sweep1d: the 1D sweep (default); 2d: batched 2D plain and split; "
-                         "ragged: mixed sizes in one graph launch")
+                         "ragged: mixed sizes in one graph launch; serve: the request stream; "
+                         "latency: single large transforms")
     ap.add_argument("--no-autotune", action="store_true", help="ragged: skip plan-time autotuning")
     ap.add_argument("--write-traffic", default="", metavar="CSV",
                     help="write profiles/traffic_<workload>.json from an ncu --csv log of "
@@ -685,6 +753,8 @@ def main():
         run_reference(args, world, rank)
     elif args.workload == "serve":
         run_serve(args, world, rank, local)
+    elif args.workload == "latency":
+        run_latency(args, world, rank, local)
     else:
         run_gpu(args, world, rank, local)
     if world > 1:

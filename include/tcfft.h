@@ -21,9 +21,9 @@
  *    hi + lo * 2^-11.  A caller with plain FP16 input passes lo = 0.
  *  - Device pointers must be 16-byte aligned.  in == out (in place) is
  *    allowed; otherwise in is never written.
- *  - Sizes: n, nx, ny powers of two with 16 <= n <= 2^24 (1D) and
- *    16 <= nx, ny <= 8192 (2D); batch >= 1.  Anything else returns
- *    TCFFT_ERR_INVALID_SIZE.
+ *  - Sizes: n, nx, ny powers of two with 16 <= n <= 2^27 (1D; 2^24 in a
+ *    ragged plan) and 16 <= nx, ny <= 8192 (2D, nx != ny allowed); batch >= 1.
+ *    Anything else returns TCFFT_ERR_INVALID_SIZE.
  *  - Errors: every call returns a status code and never aborts.  tcfft_exec
  *    is asynchronous on the given stream; a device-side failure (a bounded
  *    wait that expired) is recorded in a plan-owned status word read by
@@ -74,7 +74,8 @@ typedef enum {
 
 /* Plan a batch of `batch` 1D transforms of length n (the paper's
  * tcfftPlan1D(plan, nx, batch), Sec. 3.1).  Allocates device twiddle tables
- * and, for n > 16384, a workspace of batch*n*4 bytes (x2 for split).  On
+ * and, for n > 16384 (8192 split), a workspace of batch*n*4 bytes (x2 for
+ * split); n > 2^24 runs three passes of at most 1024 points each.  On
  * success *plan owns them until tcfft_destroy.  Not timed by benchmarks. */
 tcfft_status tcfft_plan_1d(tcfft_plan* plan, int64_t n, int64_t batch);
 

@@ -509,6 +509,10 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
   tc_fence_after_sync();
   const uint32_t tmem = *tslot;
 
+  // everything above reads only plan-time tables; the pass input may be the
+  // previous kernel's output
+  griddep_wait();
+
   int64_t chunk = blockIdx.x;
   if (p.async_load && chunk < p.nchunks) {
     issue_raw_copy<K>(p, raw_s, lbar_s, chunk_in(chunk), chunk << log2C, log2C, chunk_valid(chunk));
@@ -516,6 +520,8 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
   }
 
   for (; chunk < p.nchunks; chunk += gridDim.x) {
+    // last chunk of this CTA: the next kernel may start its prologue
+    if (chunk + gridDim.x >= p.nchunks) griddep_launch_dependents();
     const int64_t t0 = chunk << log2C;
     const int nvalid = chunk_valid(chunk);
     uint32_t* gout = p.out + side_base(p.out_l, t0, p.log2I1, p.log2I2);

@@ -21,6 +21,20 @@ constexpr int64_t kCapPlain = 32768;
 constexpr int64_t kCapSplit = 16384;
 }  // namespace
 
+cudaError_t launch_pass(const void* fn, dim3 grid, int threads, size_t smem, cudaStream_t s, void** args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
 int ilog2(int64_t v) {
   int r = 0;
   while ((int64_t(1) << r) < v) ++r;
@@ -100,6 +114,16 @@ tcfft_status geometry_try(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int6
     if (C == 0) return TCFFT_ERR_INVALID_SIZE;
     // bring small transforms up to at least one full MMA tile when possible
     while (C * L < 2048 && I1 % (2 * C) == 0 && 2 * C * L <= cap) C *= 2;
+  }
+  // small plans: fewer transforms per CTA until every SM has a chunk (down
+  // to the layout minimum), so that a single large transform spreads over
+  // the GPU and each CTA's chunk latency is short
+  {
+    int sms_now = 0, dev_now = 0;
+    cudaGetDevice(&dev_now);
+    cudaDeviceGetAttribute(&sms_now, cudaDevAttrMultiProcessorCount, dev_now);
+    const int64_t cmin = (mode == kModeContig) ? 1 : 8;
+    while (C > cmin && (T + C - 1) / C < sms_now && target_points == 0) C /= 2;
   }
   // with two or more radix-16 stages and a leading radix, every 128-row
   // MMA tile must hold one k0: C * 16^{S-1} >= 128

@@ -27,6 +27,11 @@ struct PassLaunch {
   int threads = kThreads;  // threads per CTA (a multiple of 128: one warp per TMEM lane quarter)
 };
 
+// Launches one pass kernel on `s` with programmatic stream serialization: its
+// CTAs may start their prologue while the previous kernel in the stream
+// finishes; the kernel waits (griddepcontrol.wait) before reading its input.
+cudaError_t launch_pass(const void* fn, dim3 grid, int threads, size_t smem, cudaStream_t s, void** args);
+
 int ilog2(int64_t v);
 bool is_pow2(int64_t v);
 // Integer from the environment (debugging and tuning overrides), or dflt.

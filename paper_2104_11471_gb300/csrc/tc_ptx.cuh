@@ -72,6 +72,17 @@ __device__ __forceinline__ void tc_fence_after_sync() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
+// ------------------------------------------------- programmatic dependent launch
+// Wait until the grid this one depends on (the previous kernel in the stream,
+// when launched with programmatic stream serialization) has completed and
+// its memory is visible; a no-op otherwise.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Allow the dependent grid to begin launching (its CTAs run their prologue,
+// then wait in griddep_wait until this grid has completed).
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ---------------------------------------------------------------- TMEM
 // Warp-collective: allocate `ncols` TMEM columns (power of two >= 32); the
 // TMEM base address is written to shared memory at `dst_smem`.

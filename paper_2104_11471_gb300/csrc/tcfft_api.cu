@@ -39,7 +39,8 @@ using namespace tcfft;
 
 namespace {
 
-constexpr int64_t kMaxLog2_1D = 24;
+constexpr int64_t kMaxLog2_1D = 27;       // three passes of <= 1024 points
+constexpr int64_t kMaxLog2_Ragged1D = 24;  // ragged groups use the four-step split
 constexpr int64_t kMaxLog2_2D = 13;
 
 // points per CTA on a strided side (8 transforms per CTA)
@@ -400,7 +401,11 @@ tcfft_status plan_1d(tcfft_plan_s* pl) {
     pl->ws = nullptr;
     return TCFFT_ERR_ALLOC;
   }
-  if (lg >= env_int("TCFFT_THREE_PASS_MIN", 24)) {
+  // three passes from 2^24 (tuning override TCFFT_THREE_PASS_MIN), always
+  // beyond 2^24, and for split precision beyond 2^22 (the four-step split
+  // would need strided passes longer than the split kernels' 2^11)
+  const bool three = lg >= env_int("TCFFT_THREE_PASS_MIN", 24) || lg > 24 || (pl->split && lg > 22);
+  if (three) {
     // n = N1 N2 N3 (M = N2 N3) in three passes of short transforms, so that
     // every pass keeps small per-CTA tiles with prefetch:
     //  A: N1-point DFTs of the columns x[M n1 + m], times W_n^{m k1} -> ws
@@ -622,10 +627,24 @@ tcfft_status exec_graph(tcfft_plan_s* plan, const void* in, void* out, cudaStrea
     kp.kernelParams = args;
     cudaGraphNode_t node;
     auto it = last.find(ps.group);
-    const cudaGraphNode_t* deps = (it == last.end()) ? nullptr : &it->second;
-    if (cudaGraphAddKernelNode(&node, graph, deps, deps ? 1 : 0, &kp) != cudaSuccess) {
+    if (cudaGraphAddKernelNode(&node, graph, nullptr, 0, &kp) != cudaSuccess) {
       st = TCFFT_ERR_CUDA;
       break;
+    }
+    if (it != last.end()) {
+      // programmatic edge: the pass starts its prologue while the previous
+      // pass of the group finishes and waits (griddepcontrol.wait) before
+      // reading its input; a plain edge where that is not available
+      cudaGraphEdgeData e = {};
+      e.from_port = cudaGraphKernelNodePortProgrammatic;
+      e.type = cudaGraphDependencyTypeProgrammatic;
+      if (cudaGraphAddDependencies(graph, &it->second, &node, &e, 1) != cudaSuccess) {
+        (void)cudaGetLastError();
+        if (cudaGraphAddDependencies(graph, &it->second, &node, nullptr, 1) != cudaSuccess) {
+          st = TCFFT_ERR_CUDA;
+          break;
+        }
+      }
     }
     last[ps.group] = node;
   }
@@ -679,7 +698,6 @@ tcfft_status tcfft_plan_1d_ex(tcfft_plan* plan, int64_t n, int64_t batch, tcfft_
   if ((flags & ~kPlanFlags) != 0 || (precision != TCFFT_FP16 && precision != TCFFT_FP16_SPLIT))
     return TCFFT_ERR_INVALID_VALUE;
   if (!is_pow2(n) || n < 16 || ilog2(n) > kMaxLog2_1D || batch < 1) return TCFFT_ERR_INVALID_SIZE;
-  if (precision == TCFFT_FP16_SPLIT && ilog2(n) > 22) return TCFFT_ERR_INVALID_SIZE;
   if (batch > (int64_t(1) << 40) / n) return TCFFT_ERR_INVALID_SIZE;
   tcfft_status st = check_device();
   if (st != TCFFT_OK) return st;
@@ -739,7 +757,7 @@ tcfft_status tcfft_plan_many(tcfft_plan* plan, int64_t count, const int64_t* n0,
   for (int64_t i = 0; i < count; ++i) {
     const int64_t a = n0[i], b = n1 ? n1[i] : 0;
     if (b == 0) {
-      if (!is_pow2(a) || a < 16 || ilog2(a) > kMaxLog2_1D) return TCFFT_ERR_INVALID_SIZE;
+      if (!is_pow2(a) || a < 16 || ilog2(a) > kMaxLog2_Ragged1D) return TCFFT_ERR_INVALID_SIZE;
       if (precision == TCFFT_FP16_SPLIT && ilog2(a) > 22) return TCFFT_ERR_INVALID_SIZE;
     } else {
       if (!is_pow2(a) || !is_pow2(b) || a < 16 || b < 16 || ilog2(a) > kMaxLog2_2D || ilog2(b) > kMaxLog2_2D)
@@ -775,7 +793,7 @@ tcfft_status tcfft_exec(tcfft_plan plan, const void* in, void* out, void* stream
   for (const Pass& ps : plan->passes) {
     PassParams p = bound_params(plan, ps, in, out);
     void* args[1] = {&p};
-    cudaError_t e = cudaLaunchKernel(ps.fn, ps.grid, dim3(ps.threads), args, ps.smem, s);
+    cudaError_t e = launch_pass(ps.fn, ps.grid, ps.threads, ps.smem, s, args);
     if (e != cudaSuccess) {
       if (env_int("TCFFT_DEBUG", 0))
         std::fprintf(stderr, "tcfft_exec: launch of pass (log2n %d, grid %u, smem %zu) failed: %s\n",
@@ -806,7 +824,7 @@ tcfft_status tcfft_exec_batch(tcfft_plan plan, const void* in, void* out, int64_
     if (ps.dst != BUF_WS) p.out_plane = per * batch;
     const dim3 grid((unsigned)std::min<int64_t>(p.nchunks, (int64_t)ps.grid.x));
     void* args[1] = {&p};
-    if (cudaLaunchKernel(ps.fn, grid, dim3(ps.threads), args, ps.smem, s) != cudaSuccess) return TCFFT_ERR_LAUNCH;
+    if (launch_pass(ps.fn, grid, ps.threads, ps.smem, s, args) != cudaSuccess) return TCFFT_ERR_LAUNCH;
   }
   return TCFFT_OK;
 }

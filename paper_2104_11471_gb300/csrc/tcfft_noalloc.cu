@@ -168,7 +168,7 @@ extern "C" tcfft_status tcfft_exec_1d_noalloc(int64_t n, int64_t batch, const vo
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   for (int i = 0; i < 2; ++i) {
     void* args[1] = {&ps[i].p};
-    if (cudaLaunchKernel(ps[i].fn, ps[i].grid, dim3(ps[i].threads), args, ps[i].smem, s) != cudaSuccess)
+    if (tcfft::launch_pass(ps[i].fn, ps[i].grid, ps[i].threads, ps[i].smem, s, args) != cudaSuccess)
       return TCFFT_ERR_LAUNCH;
   }
   return TCFFT_OK;

@@ -40,7 +40,7 @@ def test_status_strings(lib):
 def test_argument_checks_before_device(lib):
     h = ctypes.c_void_p()
     assert lib.tcfft_plan_1d(None, 256, 1) == 2
-    for n, b in ((100, 1), (8, 1), (1 << 25, 1), (256, 0), (256, -3)):
+    for n, b in ((100, 1), (8, 1), (1 << 28, 1), (256, 0), (256, -3)):
         assert lib.tcfft_plan_1d(ctypes.byref(h), n, b) == 1, (n, b)
     for nx, ny in ((16, 8), (8192 * 2, 16), (48, 64)):
         assert lib.tcfft_plan_2d(ctypes.byref(h), nx, ny, 1) == 1
@@ -48,6 +48,8 @@ def test_argument_checks_before_device(lib):
     assert lib.tcfft_plan_1d_ex(ctypes.byref(h), 256, 1, 0, 64) == 2  # unknown flag bit
     a = (ctypes.c_int64 * 2)(256, 100)
     assert lib.tcfft_plan_many(ctypes.byref(h), 2, a, None, 0, 0) == 1  # 100 is not a power of two
+    b = (ctypes.c_int64 * 1)(1 << 25)
+    assert lib.tcfft_plan_many(ctypes.byref(h), 1, b, None, 0, 0) == 1  # ragged 1D stops at 2^24
     assert lib.tcfft_plan_many(ctypes.byref(h), 0, a, None, 0, 0) == 1
     assert lib.tcfft_plan_many(ctypes.byref(h), 2, None, None, 0, 0) == 2
     assert lib.tcfft_exec(None, None, None, None) == 2

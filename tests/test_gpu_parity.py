@@ -176,3 +176,20 @@ def test_1d_three_pass_split(log2n, batch, monkeypatch):
     n = 1 << log2n
     got, x = fft1d_gpu(n, batch, seed=log2n + 40)
     check_rows(got, oracle.fft_batch(x), PLAIN_TOL, f"three-pass N=2^{log2n}")
+
+
+@pytest.mark.parametrize("log2n,batch,split", [(25, 2, False), (26, 1, False), (27, 1, False),
+                                               (23, 1, True), (25, 1, True)])
+def test_1d_beyond_2e24_sampled_bins(log2n, batch, split):
+    # three-pass plans past the benchmark sweep (and split precision past
+    # 2^22): sampled output bins of the first and last transform against
+    # direct FP64 sums (rel-L2 over the bins)
+    n = 1 << log2n
+    tol = SPLIT_TOL if split else PLAIN_TOL
+    rng = np.random.default_rng(log2n)
+    bins = np.unique(np.concatenate([[0, 1, n // 2, n - 1], rng.integers(0, n, size=28)]))
+    for got, xin in _full_size_rows((n,), batch, 60 + log2n, split, rows=0):
+        assert np.all(np.isfinite(got))
+        ref = oracle.dft_bins(xin, bins)
+        err = oracle.rel_l2(got[bins], ref)
+        assert err <= tol, f"N=2^{log2n} split={split}: sampled rel-L2 {err:.2e}"
