@@ -282,7 +282,7 @@ def build_sweep(args, dev, rank):
     for lg in sizes:
         n = 1 << lg
         b = POINTS // n
-        plan = tc.Plan.plan_1d(n, b)
+        plan = tc.Plan.plan_1d(n, b, tc.TCFFT_FP16, 0 if args.no_autotune else tc.TCFFT_PLAN_AUTOTUNE)
 
         def check(y=y, n=n, b=b):
             row = b // 2  # one transform from the middle of the batch
@@ -294,6 +294,7 @@ def build_sweep(args, dev, rank):
     cfg = {"workload": f"1d_sweep: N=2^8..2^24 step 2^2, batch=2^{args.log2_points}/N, "
                        "one exec per size per step, uniform[-1,1] seeded inputs",
            "sizes": [1 << s for s in sizes], "points_per_exec": POINTS, "precision": "plain FP16",
+           "geometry": "fixed planner" if args.no_autotune else "plan-time autotuner (not timed)",
            "l2": "inputs larger than L2 (1 GiB per exec), no flush"}
     cpu_sizes = [(1 << s,) for s in sizes]
     return entries, cfg, cpu_sizes, (h, None)
@@ -315,7 +316,7 @@ def build_2d(args, dev, rank):
         for side in sides:
             b = POINTS // (side * side)
             prec = tc.TCFFT_FP16_SPLIT if split else tc.TCFFT_FP16
-            plan = tc.Plan.plan_2d(side, side, b, prec)
+            plan = tc.Plan.plan_2d(side, side, b, prec, 0 if args.no_autotune else tc.TCFFT_PLAN_AUTOTUNE)
             xs = x if split else x[:2 * POINTS]
             ys = y if split else y[:2 * POINTS]
 
@@ -339,6 +340,7 @@ def build_2d(args, dev, rank):
     cfg = {"workload": f"2d: sides {sides}, batch=2^{args.log2_points}/side^2, plain FP16 and split FP16 "
                        "(hi + 2^-11 lo), one exec per (side, precision) per step, uniform[-1,1] seeded inputs",
            "points_per_exec": POINTS, "precision": "plain and split FP16",
+           "geometry": "fixed planner" if args.no_autotune else "plan-time autotuner (not timed)",
            "l2": "inputs larger than L2 (1-2 GiB per exec), no flush"}
     cpu_sizes = [(s, s) for s in sides]
     return entries, cfg, cpu_sizes, (hi, lo)
@@ -597,7 +599,7 @@ def run_gpu(args, world, rank, local):
         per.append({"exec": e.label, "launches": e.plan.num_launches, "ms": round(avg, 4),
                     "gflops": round(e.flops / (avg / 1e3) / 1e9, 1), "alg_gbs": round(gbs, 1),
                     "frac": round(gbs / peak, 4),
-                    "passes": [{k: d[k] for k in ("log2n", "mode", "per_cta", "grid", "async_load", "ctas_per_sm")}
+                    "passes": [{k: d[k] for k in ("log2n", "mode", "per_cta", "grid", "async_load", "ctas_per_sm", "threads")}
                                for d in e.plan.describe()]})
     achieved = tot_bytes / (tot_ms / 1e3) / 1e9
 
@@ -737,7 +739,8 @@ def main():
                     help="sweep1d: the 1D sweep (default); 2d: batched 2D plain and split; "
                          "ragged: mixed sizes in one graph launch; serve: the request stream; "
                          "latency: single large transforms")
-    ap.add_argument("--no-autotune", action="store_true", help="ragged: skip plan-time autotuning")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="plan with the fixed geometry heuristics instead of the plan-time autotuner")
     ap.add_argument("--write-traffic", default="", metavar="CSV",
                     help="write profiles/traffic_<workload>.json from an ncu --csv log of "
                          "dram__bytes_read.sum and dram__bytes_write.sum over pass_kernel launches of "

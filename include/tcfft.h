@@ -62,8 +62,11 @@ typedef enum {
 
 /* Plan flags (tcfft_plan_*_ex, tcfft_plan_many): */
 #define TCFFT_PLAN_AUTOTUNE 1u /* time candidate CTA geometries per pass at plan
-                                  time; picks are cached in TCFFT_TUNE_CACHE
-                                  (default $HOME/.cache/tcfft_tune.txt) */
+                                  time (points per CTA, 128 or 256 threads,
+                                  prefetching or synchronous loads; ragged
+                                  groups: points only); picks are cached in
+                                  TCFFT_TUNE_CACHE (default
+                                  $HOME/.cache/tcfft_tune.txt) */
 #define TCFFT_PLAN_GRAPH 2u    /* tcfft_exec replays one instantiated CUDA graph
                                   per (in, out) pair (captured on first use) */
 #define TCFFT_PLAN_INVERSE 4u  /* inverse transform: sign +, X[k] = sum_n x[n]

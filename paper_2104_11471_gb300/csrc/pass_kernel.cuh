@@ -76,7 +76,9 @@ struct PassCfg {
   // more resident warps hide the TMEM, barrier and memory waits).  Plain
   // lengths fit 80 registers (3 CTAs of 256 threads) without spills except
   // those with a radix-8 leading step or a single radix-16 stage after a
-  // radix 2/4 step, which keep 2.
+  // radix 2/4 step, which keep 2.  Split kernels keep their full register
+  // budget (a 128-register cap measured slower: more 128-thread CTAs of the
+  // unconstrained kernel win).
   static constexpr int MINB = SPLIT ? 1 : ((LOG2N_ % 4 == 3 || (LOG2N_ > 4 && LOG2N_ < 8)) ? 2 : 3);
   static_assert(S >= 1 && S <= 3, "pass length out of range");
 };

@@ -209,17 +209,18 @@ tcfft_status geometry_try(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int6
 }  // namespace
 
 tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int64_t I2, Side in,
-                           Side out, bool split, int64_t target_points) {
-  // The pass is latency-bound (TMEM loads, MMA completion, barriers, memory):
-  // pick the candidate with the most resident warps per SM.  A synchronous
-  // load exposes its latency and counts 0.7 of a prefetching one; at equal
-  // warps more, smaller CTAs win (fewer warps wait at each barrier).
-  // Measured at 2^28 points: N = 256 at 6 x 128 threads 0.38 ms vs 3 x 256
-  // 0.43 ms; N = 16384 at 2 x 256 synchronous 0.82 ms vs 1 x 256 prefetching
-  // 1.11 ms; 2^18 (length-512 passes) 3 x 256 prefetching 1.25 ms vs 6 x 128
-  // synchronous 1.51 ms.
-  const int thr_env = env_int("TCFFT_THREADS", 0);   // tuning override
-  const int sync_env = env_int("TCFFT_SYNC_LOAD", 0);  // debugging override
+                           Side out, bool split, int64_t target_points, int force_threads, int force_async) {
+  // The pass is latency-bound (each CTA runs a serial chain per chunk: load,
+  // then per stage MMA issue, MMA completion, TMEM loads, epilogue, barrier):
+  // pick the candidate with the most resident CTAs per SM (independent
+  // chains), a synchronous load counting 0.75 of a prefetching CTA, then the
+  // most resident warps.  Measured at 2^28 points: N = 256 at 6 x 128 threads
+  // 0.38 ms vs 3 x 256 0.43 ms; N = 16384 at 2 x 256 synchronous 0.82 ms vs
+  // 1 x 256 prefetching 1.11 ms and 2 x 128 synchronous 0.96 ms; split 4096-point
+  // rows at 3 x 128 beat 2 x 256; 2^18 (length-512 passes) 3 x 256 prefetching
+  // 1.25 ms vs 6 x 128 synchronous 1.51 ms.
+  const int thr_env = force_threads ? force_threads : env_int("TCFFT_THREADS", 0);  // tuning override
+  const int sync_env = force_async == 0 || env_int("TCFFT_SYNC_LOAD", 0);           // debugging override
   PassLaunch best;
   double best_score = -1.0;
   tcfft_status last = TCFFT_ERR_INVALID_SIZE;
@@ -227,13 +228,14 @@ tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int
     if ((thr_env == 128 || thr_env == 256) && thr != thr_env) continue;
     for (int as : {1, 0}) {
       if (as && sync_env) continue;
+      if (!as && force_async == 1) continue;
       PassLaunch c = ps;
       const tcfft_status st = geometry_try(c, L, T, I1, I2, in, out, split, target_points, thr, as);
       if (st != TCFFT_OK) {
         last = st;
         continue;
       }
-      const double score = c.occ * (thr / 32) * (as ? 1.0 : 0.7) + c.occ * 1e-3;
+      const double score = c.occ * (as ? 10.0 : 7.5) + c.occ * thr / 320.0;
       if (score > best_score) {
         best = c;
         best_score = score;

@@ -45,7 +45,11 @@ const void* pass_fn(int log2N, int mode, bool split);
 // buffers, planes and output twiddle to the caller.  Allocates nothing.
 // target_points (0 = default) overrides the points per CTA aimed at: the
 // transforms-per-CTA target of contiguous passes, the cap of strided ones.
+// target_points > 0 asks for that many points per CTA (autotuner);
+// force_threads (128 or 256) and force_async (0 or 1) fix the CTA size and
+// the load mode instead of the planner's choice.
 tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int64_t I2, Side in,
-                           Side out, bool split, int64_t target_points = 0);
+                           Side out, bool split, int64_t target_points = 0, int force_threads = 0,
+                           int force_async = -1);
 
 }  // namespace tcfft

@@ -305,7 +305,7 @@ tcfft_status tune_pass(tcfft_plan_s* pl, Pass& ps, int64_t L, int64_t T, int64_t
                        Side out, int otw_level, int log2M) {
   const int mode = (in.es == 1) ? ((out.es == 1) ? 0 : 2) : 1;
   char key[128];
-  std::snprintf(key, sizeof(key), "L%d_m%d_s%d_T%d_g%d", ilog2(L), mode, pl->split ? 1 : 0, ilog2(T),
+  std::snprintf(key, sizeof(key), "v3_L%d_m%d_s%d_T%d_g%d", ilog2(L), mode, pl->split ? 1 : 0, ilog2(T),
                 (in.toff || out.toff) ? 1 : 0);
   std::lock_guard<std::mutex> lock(g_tune_mu);
   tune_load();
@@ -329,9 +329,25 @@ tcfft_status tune_pass(tcfft_plan_s* pl, Pass& ps, int64_t L, int64_t T, int64_t
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best_ms = 1e30f;
-    for (int64_t cand : {4096, 8192, 16384, 32768}) {
+    // candidates: points per CTA (0 = the planner's) x threads per CTA x load
+    // mode; cached as points | threads << 20 | (async + 1) << 30.  Ragged
+    // groups (offset tables) run concurrently in one graph, where a geometry
+    // timed alone can lose to the planner's: they vary the points only.
+    const bool grouped = in.toff || out.toff;
+    std::vector<int64_t> cands;
+    for (int64_t pts : {0, 2048, 4096, 8192, 16384, 32768}) {
+      if (grouped) {
+        if (pts) cands.push_back(pts);
+        continue;
+      }
+      for (int64_t thr : {256, 128})
+        for (int64_t as : {1, 0}) cands.push_back(pts | (thr << 20) | ((as + 1) << 30));
+    }
+    for (int64_t cand : cands) {
       Pass c;
-      if (pass_geometry(c, L, T, I1, I2, in, out, pl->split, cand) != TCFFT_OK) continue;
+      if (pass_geometry(c, L, T, I1, I2, in, out, pl->split, cand & 0xFFFFF, (int)((cand >> 20) & 1023),
+                        (int)((cand >> 30) & 3) - 1) != TCFFT_OK)
+        continue;
       c.src = ps.src;
       c.dst = ps.dst;
       if (bind_tables(pl, c, ilog2(L), otw_level, log2M) != TCFFT_OK) continue;
@@ -361,13 +377,16 @@ tcfft_status tune_pass(tcfft_plan_s* pl, Pass& ps, int64_t L, int64_t T, int64_t
     tune_store();
   }
   Pass c;
-  if (pass_geometry(c, L, T, I1, I2, in, out, pl->split, best) != TCFFT_OK) return TCFFT_OK;
+  if (pass_geometry(c, L, T, I1, I2, in, out, pl->split, best & 0xFFFFF, (int)((best >> 20) & 1023),
+                    (int)((best >> 30) & 3) - 1) != TCFFT_OK)
+    return TCFFT_OK;
   const PassParams keep = ps.p;
   ps.fn = c.fn;
   ps.grid = c.grid;
   ps.smem = c.smem;
   ps.occ = c.occ;
   ps.regs = c.regs;
+  ps.threads = c.threads;
   ps.p = c.p;
   // tables, buffers and output twiddle stay those of the bound pass
   ps.p.tw_lo = keep.tw_lo;
@@ -894,9 +913,11 @@ size_t tcfft_plan_describe(tcfft_plan plan, char* buf, size_t len) {
     std::snprintf(tmp, sizeof(tmp),
                   "%s{\"log2n\": %d, \"mode\": \"%s\", \"transforms\": %lld, \"per_cta\": %d, "
                   "\"tiles\": %d, \"tmem_cols\": %d, \"smem\": %zu, \"async_load\": %d, \"grid\": %u, "
-                  "\"chunks\": %lld, \"out_twiddle\": %d, \"ctas_per_sm\": %d, \"regs\": %d}",
+                  "\"chunks\": %lld, \"out_twiddle\": %d, \"ctas_per_sm\": %d, \"regs\": %d, "
+                  "\"threads\": %d}",
                   i ? ", " : "", p.log2N, modes[mode], (long long)p.T, 1 << p.log2C, p.tiles, p.tmem_cols,
-                  ps.smem, p.async_load, ps.grid.x, (long long)p.nchunks, p.otw_level, ps.occ, ps.regs);
+                  ps.smem, p.async_load, ps.grid.x, (long long)p.nchunks, p.otw_level, ps.occ, ps.regs,
+                  ps.threads);
     out += tmp;
   }
   out += "]";
