@@ -268,36 +268,66 @@ def _split_draw(n_values: int, seed: int):
     return hi, lo
 
 
+DTYPES = {"fp16": "f16", "split": "f16 split (hi+lo, 3 products)", "fp32": "f32 io, f16 split (3 products)"}
+
+
+def _f32_draw(n_values: int, seed: int):
+    """n_values FP32 numbers uniform in [-1, 1] (re/im interleaved when used as complex)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-1.0, 1.0, size=n_values).astype(np.float32)
+
+
 def build_sweep(args, dev, rank):
-    """The 1D sweep: one exec per N = 2^8..2^24 over the same 2^28-point buffers."""
+    """The 1D sweep: one exec per N = 2^8..2^24 over the same 2^28-point buffers,
+    in plain FP16 (the benchmark), split FP16 or FP32 in and out."""
     import numpy as np
     import torch
     import oracle
     import paper_2104_11471_gb300 as tc
     sizes = [int(s) for s in args.sizes.split(",")] if args.sizes else SWEEP
-    h = _half_draw(2 * POINTS, 1000 + rank)
-    x = torch.from_numpy(h.view(np.uint16)).to(dev)
+    prec = args.precision
+    lo = None
+    if prec == "fp32":
+        h = _f32_draw(2 * POINTS, 1000 + rank)
+        x = torch.from_numpy(h).to(dev)
+        code, bpp, label = tc.TCFFT_FP32, 16.0, "FP32 complex in and out (split FP16 tensor-core stages)"
+    elif prec == "split":
+        h, lo = _split_draw(2 * POINTS, 1000 + rank)
+        x = torch.from_numpy(np.concatenate([h, lo]).view(np.uint16)).to(dev)
+        code, bpp, label = tc.TCFFT_FP16_SPLIT, 16.0, "split FP16 (hi + 2^-11 lo planes)"
+    else:
+        h = _half_draw(2 * POINTS, 1000 + rank)
+        x = torch.from_numpy(h.view(np.uint16)).to(dev)
+        code, bpp, label = tc.TCFFT_FP16, 8.0, "plain FP16"
     y = torch.empty_like(x)
     entries = []
     for lg in sizes:
         n = 1 << lg
         b = POINTS // n
-        plan = tc.Plan.plan_1d(n, b, tc.TCFFT_FP16, 0 if args.no_autotune else tc.TCFFT_PLAN_AUTOTUNE)
+        plan = tc.Plan.plan_1d(n, b, code, 0 if args.no_autotune else tc.TCFFT_PLAN_AUTOTUNE)
 
         def check(y=y, n=n, b=b):
             row = b // 2  # one transform from the middle of the batch
-            xin = h[row * 2 * n:(row + 1) * 2 * n].astype(np.float64)
-            out = y[row * 2 * n:(row + 1) * 2 * n].cpu().numpy().view(np.float16).astype(np.float64)
+            sl = slice(row * 2 * n, (row + 1) * 2 * n)
+            xin = h[sl].astype(np.float64)
+            if prec == "fp32":
+                out = y[sl].cpu().numpy().astype(np.float64)
+            else:
+                out = y[sl].cpu().numpy().view(np.float16).astype(np.float64)
+            if prec == "split":
+                xin = xin + lo[sl].astype(np.float64) / 2048.0
+                out = out + y[2 * POINTS:][sl].cpu().numpy().view(np.float16).astype(np.float64) / 2048.0
             ref = oracle.fft_batch((xin[0::2] + 1j * xin[1::2])[None, :])[0]
             return oracle.rel_l2(out[0::2] + 1j * out[1::2], ref)
-        entries.append(Entry(f"1d n={n} batch={b}", plan, x, y, flops_1d(n, b), 8.0 * n * b, check))
+        entries.append(Entry(f"1d n={n} batch={b}", plan, x, y, flops_1d(n, b), bpp * n * b, check))
     cfg = {"workload": f"1d_sweep: N=2^8..2^24 step 2^2, batch=2^{args.log2_points}/N, "
                        "one exec per size per step, uniform[-1,1] seeded inputs",
-           "sizes": [1 << s for s in sizes], "points_per_exec": POINTS, "precision": "plain FP16",
+           "sizes": [1 << s for s in sizes], "points_per_exec": POINTS, "precision": label,
            "geometry": "fixed planner" if args.no_autotune else "plan-time autotuner (not timed)",
            "l2": "inputs larger than L2 (1 GiB per exec), no flush"}
     cpu_sizes = [(1 << s,) for s in sizes]
-    return entries, cfg, cpu_sizes, (h, None)
+    return entries, cfg, cpu_sizes, (h, lo)
 
 
 def build_2d(args, dev, rank):
@@ -413,7 +443,7 @@ def build_ragged(args, dev, rank):
         return {"ms_per_step": round(ms, 4), "gflops": round(flops / (ms / 1e3) / 1e9, 1),
                 "launches_per_step": launches}
     cpu_sizes = [sh for sh in shapes[:64]]
-    return entries, cfg, cpu_sizes, (h, None), per_size_launches
+    return entries, cfg, cpu_sizes, (h, lo), per_size_launches
 
 
 def run_serve(args, world, rank, local):
@@ -641,7 +671,8 @@ def run_gpu(args, world, rank, local):
         cpu = {"value": f / s_ / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
 
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", f"traffic_{args.workload}.json")
+    suffix = "" if args.precision == "fp16" else f"_{args.precision}"
+    tpath = os.path.join(ROOT, "profiles", f"traffic_{args.workload}{suffix}.json")
     if os.path.exists(tpath):
         try:
             with open(tpath) as f:
@@ -658,7 +689,7 @@ def run_gpu(args, world, rank, local):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision] if args.workload == "sweep1d" else "f16", "data": "synthetic",
         "config": cfg,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
@@ -702,7 +733,8 @@ def write_traffic(args):
            "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum over the pass_kernel launches of the "
                    "timed step, scaled to 2^28 points per exec (every launch reads and writes its data "
                    "once, so traffic grows in proportion)"}
-    path = os.path.join(ROOT, "profiles", f"traffic_{args.workload}.json")
+    suffix = "" if args.precision == "fp16" else f"_{args.precision}"
+    path = os.path.join(ROOT, "profiles", f"traffic_{args.workload}{suffix}.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
         f.write("\n")
@@ -739,6 +771,8 @@ def main():
                     help="sweep1d: the 1D sweep (default); 2d: batched 2D plain and split; "
                          "ragged: mixed sizes in one graph launch; serve: the request stream; "
                          "latency: single large transforms")
+    ap.add_argument("--precision", default="fp16", choices=["fp16", "split", "fp32"],
+                    help="sweep1d: plain FP16 (the benchmark), split FP16, or FP32 in and out")
     ap.add_argument("--no-autotune", action="store_true",
                     help="plan with the fixed geometry heuristics instead of the plan-time autotuner")
     ap.add_argument("--write-traffic", default="", metavar="CSV",

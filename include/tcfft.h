@@ -19,6 +19,8 @@
  *  - Split precision (TCFFT_FP16_SPLIT): one buffer holding two planes laid
  *    out like the plain data, plane 0 = hi, plane 1 = lo; the value is
  *    hi + lo * 2^-11.  A caller with plain FP16 input passes lo = 0.
+ *  - TCFFT_FP32: interleaved FP32 complex (re, im), 8 bytes per point, in the
+ *    same element order as the plain data.
  *  - Device pointers must be 16-byte aligned.  in == out (in place) is
  *    allowed; otherwise in is never written.
  *  - Sizes: n, nx, ny powers of two with 16 <= n <= 2^27 (1D; 2^24 in a
@@ -57,7 +59,15 @@ typedef enum {
 
 typedef enum {
   TCFFT_FP16 = 0,       /* FP16 storage and operands, FP32 accumulation */
-  TCFFT_FP16_SPLIT = 1  /* hi + 2^-11 lo pairs, three MMA products per stage */
+  TCFFT_FP16_SPLIT = 1, /* hi + 2^-11 lo pairs, three MMA products per stage */
+  TCFFT_FP32 = 2        /* interleaved FP32 complex in and out (8 B per point):
+                           each value is split into hi + 2^-11 lo FP16 on load,
+                           the stages run as TCFFT_FP16_SPLIT (FP16 operands,
+                           three products, FP32 accumulation) and the FP32
+                           accumulator is stored as is.  About 22 significant
+                           bits; input values and intermediates must stay
+                           within FP16 range (|x| < 65504, as in the other
+                           precisions) */
 } tcfft_precision;
 
 /* Plan flags (tcfft_plan_*_ex, tcfft_plan_many): */
@@ -77,7 +87,7 @@ typedef enum {
 
 /* Plan a batch of `batch` 1D transforms of length n (the paper's
  * tcfftPlan1D(plan, nx, batch), Sec. 3.1).  Allocates device twiddle tables
- * and, for n > 16384 (8192 split), a workspace of batch*n*4 bytes (x2 for
+ * and, for n > 16384, a workspace of batch*n*4 bytes (x2 for
  * split); n > 2^24 runs three passes of at most 1024 points each.  On
  * success *plan owns them until tcfft_destroy.  Not timed by benchmarks. */
 tcfft_status tcfft_plan_1d(tcfft_plan* plan, int64_t n, int64_t batch);

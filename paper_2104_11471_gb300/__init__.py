@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libtcfft.so")
 
 TCFFT_FP16 = 0
 TCFFT_FP16_SPLIT = 1
+TCFFT_FP32 = 2          # interleaved FP32 complex in and out (split FP16 tensor-core stages)
 TCFFT_PLAN_AUTOTUNE = 1
 TCFFT_PLAN_GRAPH = 2
 TCFFT_PLAN_INVERSE = 4

@@ -214,6 +214,17 @@ __device__ __forceinline__ uint32_t stg_key(uint32_t c, uint32_t ko, int log2C) 
   }
 }
 
+// 32-bit words per point on a side: 2 for interleaved FP32 complex (split
+// kernels with in_f32 / out_f32), else 1 (FP16 complex or one FP16 plane)
+template <class K>
+__device__ __forceinline__ uint32_t in_words(const PassParams& p) {
+  return (K::SPLIT && p.in_f32) ? 2u : 1u;
+}
+template <class K>
+__device__ __forceinline__ uint32_t out_words(const PassParams& p) {
+  return (K::SPLIT && p.out_f32) ? 2u : 1u;
+}
+
 // ------------------------------------------------------------------ loads
 __device__ __forceinline__ void cp_async16(uint32_t dst_smem, const void* src, uint32_t src_bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst_smem), "l"(src),
@@ -237,8 +248,12 @@ __device__ __forceinline__ void issue_raw_copy(const PassParams& p, uint32_t raw
       if (threadIdx.x == 0) {
         const uint32_t bytes = ((uint32_t)nvalid << K::LOG2N) * 4u;
         mbar_arrive_expect_tx(lbar, bytes * K::PLANES);
-        bulk_g2s(raw_s, gin, bytes, lbar);
-        if constexpr (K::SPLIT) bulk_g2s(raw_s + P * 4u, gin + p.in_plane, bytes, lbar);
+        if (K::SPLIT && p.in_f32) {
+          bulk_g2s(raw_s, gin, bytes * 2u, lbar);  // FP32 complex: raw[c*N + e] at 8 B per point
+        } else {
+          bulk_g2s(raw_s, gin, bytes, lbar);
+          if constexpr (K::SPLIT) bulk_g2s(raw_s + P * 4u, gin + p.in_plane, bytes, lbar);
+        }
       }
     } else if (threadIdx.x < 32) {
       // one bulk copy per transform, from its own offset (ragged batches)
@@ -246,11 +261,24 @@ __device__ __forceinline__ void issue_raw_copy(const PassParams& p, uint32_t raw
       if (threadIdx.x == 0) mbar_arrive_expect_tx(lbar, bytes * K::PLANES * (uint32_t)nvalid);
       __syncwarp();
       for (int c = threadIdx.x; c < nvalid; c += 32) {
-        const uint32_t* src = p.in + side_base(p.in_l, t0 + c, p.log2I1, p.log2I2);
-        bulk_g2s(raw_s + (uint32_t)c * bytes, src, bytes, lbar);
-        if constexpr (K::SPLIT) bulk_g2s(raw_s + P * 4u + (uint32_t)c * bytes, src + p.in_plane, bytes, lbar);
+        const uint32_t* src = p.in + in_words<K>(p) * side_base(p.in_l, t0 + c, p.log2I1, p.log2I2);
+        if (K::SPLIT && p.in_f32) {
+          bulk_g2s(raw_s + (uint32_t)c * bytes * 2u, src, bytes * 2u, lbar);
+        } else {
+          bulk_g2s(raw_s + (uint32_t)c * bytes, src, bytes, lbar);
+          if constexpr (K::SPLIT) bulk_g2s(raw_s + P * 4u + (uint32_t)c * bytes, src + p.in_plane, bytes, lbar);
+        }
       }
     }
+  } else if (K::SPLIT && p.in_f32) {
+    // FP32 complex: 16-byte copies of two adjacent columns, raw[e*C + c] at 8 B per point
+    const uint32_t nq = P >> 1;
+    const int cq = log2C - 1;
+    for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x) {
+      const uint32_t off = (q >> cq) * p.in_l.es + ((q & ((1u << cq) - 1u)) << 1);
+      cp_async16(raw_s + (q << 4), gin + 2u * off, 16);
+    }
+    cp_async_commit();
   } else {
     const uint32_t nq = P >> 2;  // 16-byte chunks per plane
     const int cq = log2C - 2;
@@ -298,7 +326,7 @@ __device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, con
         valid = c < nvalid;
         if (p.in_gather && valid) {
           // ragged batch read from global memory: transform c has its own offset
-          src = p.in + side_base(p.in_l, t0 + c, p.log2I1, p.log2I2);
+          src = p.in + in_words<K>(p) * side_base(p.in_l, t0 + c, p.log2I1, p.log2I2);
           src_lo = src + p.in_plane;
           off0 = np;
         }
@@ -311,6 +339,28 @@ __device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, con
       step = (uint32_t)K::L * es;
     }
     uint32_t hv[RX][8], lv[RX][8];
+    if (K::SPLIT && p.in_f32) {
+      // interleaved FP32 complex (shared or global memory, 8 B per point):
+      // split each value into hi = fp16(v), lo = fp16((v - hi) 2^11)
+      const float* srcf = reinterpret_cast<const float*>(src);
+#pragma unroll
+      for (int n0 = 0; n0 < RX; ++n0) {
+        const float4* f4 = reinterpret_cast<const float4*>(srcf + 2u * (off0 + n0 * step));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float4 f = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          if constexpr (SMEM) {
+            f = f4[q];
+          } else if (valid) {
+            f = __ldg(f4 + q);
+          }
+          hv[n0][2 * q] = f2h2(f.x, f.y);
+          lv[n0][2 * q] = split_lo(f.x, f.y, hv[n0][2 * q]);
+          hv[n0][2 * q + 1] = f2h2(f.z, f.w);
+          lv[n0][2 * q + 1] = split_lo(f.z, f.w, hv[n0][2 * q + 1]);
+        }
+      }
+    } else {
 #pragma unroll
     for (int n0 = 0; n0 < RX; ++n0) {
       uint4 a = make_uint4(0, 0, 0, 0), b = a;
@@ -337,6 +387,7 @@ __device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, con
         lv[n0][0] = c2.x; lv[n0][1] = c2.y; lv[n0][2] = c2.z; lv[n0][3] = c2.w;
         lv[n0][4] = d.x; lv[n0][5] = d.y; lv[n0][6] = d.z; lv[n0][7] = d.w;
       }
+    }
     }
     if (p.conj_in) {
       // inverse transform: conj(x) on the way in (sign bit of each imaginary half)
@@ -499,7 +550,7 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
   bool ok = true, pending = false;  // pending: a bulk copy into RAW is in flight
 
   auto chunk_in = [&](int64_t ch) {
-    return p.in + side_base(p.in_l, ch << log2C, p.log2I1, p.log2I2);
+    return p.in + in_words<K>(p) * side_base(p.in_l, ch << log2C, p.log2I1, p.log2I2);
   };
   auto chunk_valid = [&](int64_t ch) {
     const int64_t left = p.T - (ch << log2C);
@@ -526,7 +577,8 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
     if (chunk + gridDim.x >= p.nchunks) griddep_launch_dependents();
     const int64_t t0 = chunk << log2C;
     const int nvalid = chunk_valid(chunk);
-    uint32_t* gout = p.out + side_base(p.out_l, t0, p.log2I1, p.log2I2);
+    const uint32_t ow = out_words<K>(p);
+    uint32_t* gout = p.out + ow * side_base(p.out_l, t0, p.log2I1, p.log2I2);
 
     if (p.async_load) {
       if constexpr (K::IN_C) {
@@ -752,8 +804,18 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
           if constexpr (K::DIRECT_OUT) {
             // lanes hold consecutive output indices: store straight to global
             if ((int)c < nvalid) {
-              uint32_t* o = (p.out_scatter ? p.out + side_base(p.out_l, t0 + c, p.log2I1, p.log2I2)
-                                           : gout + (c << LOG2N)) + kbase;
+              uint32_t* o = (p.out_scatter ? p.out + ow * side_base(p.out_l, t0 + c, p.log2I1, p.log2I2)
+                                           : gout + ow * (c << LOG2N)) + ow * kbase;
+              if (SPLIT && p.out_f32) {
+                // interleaved FP32 complex straight from the accumulator
+                float2* of = reinterpret_cast<float2*>(o);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                  of[(2 * i) * kstep] = make_float2(X[i].x, Y[i].x);
+                  of[(2 * i + 1) * kstep] = make_float2(X[i].y, Y[i].y);
+                }
+                continue;
+              }
 #pragma unroll
               for (int i = 0; i < 8; ++i) {
                 const uint32_t h0 = f2h2(X[i].x, Y[i].x), h1 = f2h2(X[i].y, Y[i].y);
@@ -775,6 +837,14 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
           for (int i = 0; i < 8; ++i) {
             const uint32_t i0 = (base + (2 * i) * wstep) ^ key;
             const uint32_t i1 = (base + (2 * i + 1) * wstep) ^ key;
+            if (SPLIT && p.out_f32) {
+              // FP32 output: the two staging planes hold re and im
+              stg[i0] = __float_as_uint(X[i].x);
+              stg[i1] = __float_as_uint(X[i].y);
+              stg[P + i0] = __float_as_uint(Y[i].x);
+              stg[P + i1] = __float_as_uint(Y[i].y);
+              continue;
+            }
             const uint32_t h0 = f2h2(X[i].x, Y[i].x), h1 = f2h2(X[i].y, Y[i].y);
             stg[i0] = h0;
             stg[i1] = h1;
@@ -801,8 +871,15 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
           const uint32_t c = (q << 2) >> LOG2N;
           const uint32_t ko = (q << 2) & (K::N - 1);
           const uint32_t pq = q ^ stg_key<K>(c, ko, log2C);
-          uint32_t* o = p.out_scatter ? p.out + side_base(p.out_l, t0 + c, p.log2I1, p.log2I2) + ko
-                                      : gout + (q << 2);
+          uint32_t* o = p.out_scatter ? p.out + ow * (side_base(p.out_l, t0 + c, p.log2I1, p.log2I2) + ko)
+                                      : gout + ow * (q << 2);
+          if (SPLIT && p.out_f32) {
+            // four points: re and im planes -> interleaved FP32 complex
+            const uint4 re = stg[pq], im = stg[nch + pq];
+            reinterpret_cast<uint4*>(o)[0] = make_uint4(re.x, im.x, re.y, im.y);
+            reinterpret_cast<uint4*>(o)[1] = make_uint4(re.z, im.z, re.w, im.w);
+            continue;
+          }
           *reinterpret_cast<uint4*>(o) = stg[pq];
           if constexpr (SPLIT) *reinterpret_cast<uint4*>(o + p.out_plane) = stg[nch + pq];
         }
@@ -814,6 +891,13 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
           const uint32_t cc = (q & ((1u << cq) - 1u)) << 2;
           const uint32_t off = ko * es + cc;
           const uint32_t pq = q ^ stg_key<K>(cc, ko, log2C);
+          if (SPLIT && p.out_f32) {
+            const uint4 re = stg[pq], im = stg[nch + pq];
+            uint4* o = reinterpret_cast<uint4*>(gout + 2u * off);
+            o[0] = make_uint4(re.x, im.x, re.y, im.y);
+            o[1] = make_uint4(re.z, im.z, re.w, im.w);
+            continue;
+          }
           *reinterpret_cast<uint4*>(gout + off) = stg[pq];
           if constexpr (SPLIT) *reinterpret_cast<uint4*>(gout + p.out_plane + off) = stg[nch + pq];
         }

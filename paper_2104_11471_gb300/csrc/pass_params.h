@@ -61,6 +61,10 @@ struct PassParams {
   int conj_in;            // negate imaginary parts on load (first pass of an inverse)
   int conj_out;           // negate imaginary parts of the results (last pass of an inverse)
   float prescale;         // factor on the leading radix-R step (1/R when the pass is scaled)
+  // split kernels only: this side is interleaved FP32 complex (8 B per point,
+  // one buffer) instead of the hi / lo FP16 planes; offsets stay in points
+  int in_f32;
+  int out_f32;
   int in_gather;          // contiguous input, one offset per transform (see SideLayout)
   int out_scatter;        // contiguous output, one offset per transform
   int async_load;         // 1: prefetch the next chunk with cp.async into a raw buffer
@@ -81,7 +85,7 @@ constexpr int kDevErrTimeout = 5;
 // Supported pass lengths per mode and precision (log2 N).
 constexpr int kMinLog2Pass = 4;
 constexpr int max_log2_pass(int mode, bool split) {
-  return mode == kModeContig ? (split ? 13 : 14) : (split ? 11 : 12);
+  return mode == kModeContig ? 14 : (split ? 11 : 12);
 }
 
 }  // namespace tcfft

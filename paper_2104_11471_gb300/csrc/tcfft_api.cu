@@ -48,7 +48,7 @@ constexpr int64_t kCapPlain = 32768;
 constexpr int64_t kCapSplit = 16384;
 // largest single-pass transform (contiguous side)
 constexpr int64_t kSinglePlain = 16384;
-constexpr int64_t kSingleSplit = 8192;
+constexpr int64_t kSingleSplit = 16384;
 
 enum Buf { BUF_IN = 0, BUF_OUT = 1, BUF_WS = 2 };
 
@@ -82,6 +82,7 @@ struct tcfft_plan_s {
   int dims = 1;
   int64_t n = 0, nx = 0, ny = 0, batch = 0;
   bool split = false;
+  bool fp32 = false;  // TCFFT_FP32: user buffers are interleaved FP32 complex (split kernels inside)
   int64_t points = 0;  // total complex points per plane
   std::vector<Pass> passes;
   std::map<int, TwTable> tables;
@@ -582,6 +583,25 @@ void apply_direction(tcfft_plan_s* pl) {
   }
 }
 
+// TCFFT_FP32 plans run the split kernels; every pass side on a user buffer
+// (input or output, which 2D plans also use between their passes) reads or
+// writes interleaved FP32 complex, the workspace keeps the hi / lo planes.
+void apply_io(tcfft_plan_s* pl) {
+  for (Pass& ps : pl->passes) {
+    ps.p.in_f32 = (pl->fp32 && ps.src != BUF_WS) ? 1 : 0;
+    ps.p.out_f32 = (pl->fp32 && ps.dst != BUF_WS) ? 1 : 0;
+  }
+}
+
+bool valid_precision(tcfft_precision pr) {
+  return pr == TCFFT_FP16 || pr == TCFFT_FP16_SPLIT || pr == TCFFT_FP32;
+}
+
+void set_precision(tcfft_plan_s* pl, tcfft_precision pr) {
+  pl->split = pr != TCFFT_FP16;
+  pl->fp32 = pr == TCFFT_FP32;
+}
+
 tcfft_status check_device() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return TCFFT_ERR_UNSUPPORTED;
@@ -714,8 +734,7 @@ tcfft_status tcfft_plan_1d_ex(tcfft_plan* plan, int64_t n, int64_t batch, tcfft_
                               unsigned flags) {
   if (!plan) return TCFFT_ERR_INVALID_VALUE;
   *plan = nullptr;
-  if ((flags & ~kPlanFlags) != 0 || (precision != TCFFT_FP16 && precision != TCFFT_FP16_SPLIT))
-    return TCFFT_ERR_INVALID_VALUE;
+  if ((flags & ~kPlanFlags) != 0 || !valid_precision(precision)) return TCFFT_ERR_INVALID_VALUE;
   if (!is_pow2(n) || n < 16 || ilog2(n) > kMaxLog2_1D || batch < 1) return TCFFT_ERR_INVALID_SIZE;
   if (batch > (int64_t(1) << 40) / n) return TCFFT_ERR_INVALID_SIZE;
   tcfft_status st = check_device();
@@ -725,12 +744,13 @@ tcfft_status tcfft_plan_1d_ex(tcfft_plan* plan, int64_t n, int64_t batch, tcfft_
   pl->dims = 1;
   pl->n = n;
   pl->batch = batch;
-  pl->split = precision == TCFFT_FP16_SPLIT;
+  set_precision(pl, precision);
   pl->points = n * batch;
   apply_flags(pl, flags);
   st = common_init(pl);
   if (st == TCFFT_OK) st = plan_1d(pl);
   if (st == TCFFT_OK) apply_direction(pl);
+  if (st == TCFFT_OK) apply_io(pl);
   return finish(pl, st, plan);
 }
 
@@ -742,8 +762,7 @@ tcfft_status tcfft_plan_2d_ex(tcfft_plan* plan, int64_t nx, int64_t ny, int64_t 
                               tcfft_precision precision, unsigned flags) {
   if (!plan) return TCFFT_ERR_INVALID_VALUE;
   *plan = nullptr;
-  if ((flags & ~kPlanFlags) != 0 || (precision != TCFFT_FP16 && precision != TCFFT_FP16_SPLIT))
-    return TCFFT_ERR_INVALID_VALUE;
+  if ((flags & ~kPlanFlags) != 0 || !valid_precision(precision)) return TCFFT_ERR_INVALID_VALUE;
   if (!is_pow2(nx) || !is_pow2(ny) || nx < 16 || ny < 16 || ilog2(nx) > kMaxLog2_2D ||
       ilog2(ny) > kMaxLog2_2D || batch < 1)
     return TCFFT_ERR_INVALID_SIZE;
@@ -756,12 +775,13 @@ tcfft_status tcfft_plan_2d_ex(tcfft_plan* plan, int64_t nx, int64_t ny, int64_t 
   pl->nx = nx;
   pl->ny = ny;
   pl->batch = batch;
-  pl->split = precision == TCFFT_FP16_SPLIT;
+  set_precision(pl, precision);
   pl->points = nx * ny * batch;
   apply_flags(pl, flags);
   st = common_init(pl);
   if (st == TCFFT_OK) st = plan_2d(pl);
   if (st == TCFFT_OK) apply_direction(pl);
+  if (st == TCFFT_OK) apply_io(pl);
   return finish(pl, st, plan);
 }
 
@@ -769,15 +789,14 @@ tcfft_status tcfft_plan_many(tcfft_plan* plan, int64_t count, const int64_t* n0,
                              tcfft_precision precision, unsigned flags) {
   if (!plan) return TCFFT_ERR_INVALID_VALUE;
   *plan = nullptr;
-  if (!n0 || (flags & ~kPlanFlags) != 0 || (precision != TCFFT_FP16 && precision != TCFFT_FP16_SPLIT))
-    return TCFFT_ERR_INVALID_VALUE;
+  if (!n0 || (flags & ~kPlanFlags) != 0 || !valid_precision(precision)) return TCFFT_ERR_INVALID_VALUE;
   if (count < 1 || count > (int64_t(1) << 24)) return TCFFT_ERR_INVALID_SIZE;
   int64_t total = 0;
   for (int64_t i = 0; i < count; ++i) {
     const int64_t a = n0[i], b = n1 ? n1[i] : 0;
     if (b == 0) {
       if (!is_pow2(a) || a < 16 || ilog2(a) > kMaxLog2_Ragged1D) return TCFFT_ERR_INVALID_SIZE;
-      if (precision == TCFFT_FP16_SPLIT && ilog2(a) > 22) return TCFFT_ERR_INVALID_SIZE;
+      if (precision != TCFFT_FP16 && ilog2(a) > 22) return TCFFT_ERR_INVALID_SIZE;
     } else {
       if (!is_pow2(a) || !is_pow2(b) || a < 16 || b < 16 || ilog2(a) > kMaxLog2_2D || ilog2(b) > kMaxLog2_2D)
         return TCFFT_ERR_INVALID_SIZE;
@@ -791,11 +810,12 @@ tcfft_status tcfft_plan_many(tcfft_plan* plan, int64_t count, const int64_t* n0,
   if (!pl) return TCFFT_ERR_ALLOC;
   pl->dims = 0;
   pl->batch = count;
-  pl->split = precision == TCFFT_FP16_SPLIT;
+  set_precision(pl, precision);
   apply_flags(pl, flags);
   st = common_init(pl);
   if (st == TCFFT_OK) st = plan_many(pl, count, n0, n1);
   if (st == TCFFT_OK) apply_direction(pl);
+  if (st == TCFFT_OK) apply_io(pl);
   return finish(pl, st, plan);
 }
 

@@ -62,6 +62,15 @@ def split_input(shape, seed: int) -> tuple[np.ndarray, np.ndarray]:
     return split_planes(uniform_complex(shape, seed))
 
 
+def float32_input(shape, seed: int) -> np.ndarray:
+    """The FP32-precision input: interleaved FP32 complex [..., 2] (round to nearest)."""
+    z = uniform_complex(shape, seed)
+    out = np.empty(z.shape + (2,), dtype=np.float32)
+    out[..., 0] = z.real.astype(np.float32)
+    out[..., 1] = z.imag.astype(np.float32)
+    return out
+
+
 def sweep_seed(log2n: int) -> int:
     """Seed of the 1D sweep at N = 2^log2n."""
     return 1000 + log2n

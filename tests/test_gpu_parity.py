@@ -52,7 +52,7 @@ def test_2d_sizes(nx, ny, batch):
     check_rows(got.reshape(batch, -1), ref.reshape(batch, -1), PLAIN_TOL, f"2D {nx}x{ny}")
 
 
-@pytest.mark.parametrize("log2n", [4, 8, 11, 12, 13, 16])
+@pytest.mark.parametrize("log2n", [4, 8, 11, 12, 13, 14, 16])
 def test_1d_split_precision(log2n):
     n = 1 << log2n
     got, x = fft1d_gpu(n, 3, seed=50 + log2n, split=True)
