@@ -270,6 +270,23 @@ __device__ __forceinline__ void issue_raw_copy(const PassParams& p, uint32_t raw
         }
       }
     }
+  } else if (p.in_tma) {
+    // tensor-map boxes of C columns x up to 256 elements per plane, issued by
+    // one thread; completion on `lbar` like the contiguous copies
+    if (threadIdx.x == 0) {
+      const uint32_t wpp = in_words<K>(p);  // 32-bit words per point of a plane
+      const uint32_t planes = (K::SPLIT && !p.in_f32) ? 2u : 1u;
+      mbar_arrive_expect_tx(lbar, P * 4u * wpp * planes);
+      const int bl = K::N < 256 ? K::N : 256;
+      const int64_t t1 = t0 & ((int64_t(1) << p.log2I1) - 1);
+      const int64_t t23 = t0 >> p.log2I1;
+      const int t2 = (int)(t23 & ((int64_t(1) << p.log2I2) - 1));
+      const int t3 = (int)(t23 >> p.log2I2);
+      for (uint32_t pl = 0; pl < planes; ++pl)
+        for (int e0 = 0; e0 < K::N; e0 += bl)
+          tma_load_5d(raw_s + pl * (P * 4u) + (uint32_t)e0 * ((uint32_t)1 << log2C) * 4u * wpp, &p.in_map,
+                      (int)t1, e0, t2, t3, (int)pl, lbar);
+    }
   } else if (K::SPLIT && p.in_f32) {
     // FP32 complex: 16-byte copies of two adjacent columns, raw[e*C + c] at 8 B per point
     const uint32_t nq = P >> 1;
@@ -569,7 +586,7 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
   int64_t chunk = blockIdx.x;
   if (p.async_load && chunk < p.nchunks) {
     issue_raw_copy<K>(p, raw_s, lbar_s, chunk_in(chunk), chunk << log2C, log2C, chunk_valid(chunk));
-    pending = K::IN_C;
+    pending = K::IN_C || p.in_tma;
   }
 
   for (; chunk < p.nchunks; chunk += gridDim.x) {
@@ -581,7 +598,7 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
     uint32_t* gout = p.out + ow * side_base(p.out_l, t0, p.log2I1, p.log2I2);
 
     if (p.async_load) {
-      if constexpr (K::IN_C) {
+      if (K::IN_C || p.in_tma) {
         const bool got = mbar_wait_bounded(lbar_s, lphase, kWaitLimitCycles);
         if (got) {
           lphase ^= 1u;
@@ -601,7 +618,7 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
       const int64_t next = chunk + gridDim.x;
       if (next < p.nchunks) {
         issue_raw_copy<K>(p, raw_s, lbar_s, chunk_in(next), next << log2C, log2C, chunk_valid(next));
-        pending = K::IN_C;
+        pending = K::IN_C || p.in_tma;
       }
     } else {
       const uint32_t* gin = chunk_in(chunk);
@@ -908,7 +925,7 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
 
   // unwind: no copy may still target this CTA's shared memory when it exits
   if (p.async_load) {
-    if constexpr (K::IN_C) {
+    if (K::IN_C || p.in_tma) {
       if (pending) (void)mbar_wait_bounded(lbar_s, lphase, kWaitLimitCycles);
     } else {
       cp_async_wait_all();

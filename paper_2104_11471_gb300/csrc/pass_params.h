@@ -2,6 +2,8 @@
 // single kernel launch computes entirely on chip (shared memory + TMEM).
 // Host code (planner) and device code (pass kernel) both include this file.
 #pragma once
+#include <cuda.h>  // CUtensorMap
+
 #include <cstdint>
 
 namespace tcfft {
@@ -65,6 +67,12 @@ struct PassParams {
   // one buffer) instead of the hi / lo FP16 planes; offsets stay in points
   int in_f32;
   int out_f32;
+  // strided input through the tensor-memory accelerator: one tensor map of
+  // the input side (dims t1, element, t2, t3, plane; boxes of C x <= 256
+  // elements), encoded at exec time for the bound pointer; 0 = per-thread
+  // 16-byte cp.async gathers
+  int in_tma;
+  alignas(64) CUtensorMap in_map;
   int in_gather;          // contiguous input, one offset per transform (see SideLayout)
   int out_scatter;        // contiguous output, one offset per transform
   int async_load;         // 1: prefetch the next chunk with cp.async into a raw buffer

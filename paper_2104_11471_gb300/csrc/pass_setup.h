@@ -32,6 +32,12 @@ struct PassLaunch {
 // finishes; the kernel waits (griddepcontrol.wait) before reading its input.
 cudaError_t launch_pass(const void* fn, dim3 grid, int threads, size_t smem, cudaStream_t s, void** args);
 
+// Encodes p.in_map for the input pointer bound in p (strided-input passes
+// planned with p.in_tma); clears p.in_tma when the map cannot be encoded, and
+// the kernel then gathers with per-thread 16-byte copies.  Call after every
+// change of p.in, p.T or p.in_plane.
+void encode_in_map(PassParams& p, bool split);
+
 int ilog2(int64_t v);
 bool is_pow2(int64_t v);
 // Integer from the environment (debugging and tuning overrides), or dflt.

@@ -354,6 +354,7 @@ tcfft_status tune_pass(tcfft_plan_s* pl, Pass& ps, int64_t L, int64_t T, int64_t
       if (bind_tables(pl, c, ilog2(L), otw_level, log2M) != TCFFT_OK) continue;
       c.p.in = reinterpret_cast<const uint32_t*>(pl->tune_buf);
       c.p.out = reinterpret_cast<uint32_t*>(pl->tune_buf);
+      encode_in_map(c.p, pl->split);
       void* args[1] = {&c.p};
       float ms = 0.0f;
       bool okc = true;
@@ -641,6 +642,7 @@ PassParams bound_params(const tcfft_plan_s* plan, const Pass& ps, const void* in
                        reinterpret_cast<uint32_t*>(out), reinterpret_cast<uint32_t*>(plan->ws)};
   p.in = bufs[ps.src] + (ps.src == BUF_WS ? ps.src_off : 0);
   p.out = bufs[ps.dst] + (ps.dst == BUF_WS ? ps.dst_off : 0);
+  encode_in_map(p, plan->split);
   return p;
 }
 
@@ -862,6 +864,8 @@ tcfft_status tcfft_exec_batch(tcfft_plan plan, const void* in, void* out, int64_
     if (ps.src != BUF_WS) p.in_plane = per * batch;
     if (ps.dst != BUF_WS) p.out_plane = per * batch;
     const dim3 grid((unsigned)std::min<int64_t>(p.nchunks, (int64_t)ps.grid.x));
+    p.in_tma = ps.p.in_tma;  // re-encode for the shorter batch
+    encode_in_map(p, plan->split);
     void* args[1] = {&p};
     if (launch_pass(ps.fn, grid, ps.threads, ps.smem, s, args) != cudaSuccess) return TCFFT_ERR_LAUNCH;
   }
