@@ -537,15 +537,17 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
   const int half = warp >> 2;    // which tiles this warp takes in the epilogue
   const int halves = (int)(blockDim.x >> 7);  // warps per TMEM lane quarter
 
-  // DFT matrix images -> shared memory: hi images k0 = 0..NB-1, then (split)
-  // the lo images; the global table holds 8 hi then 8 lo images.
+  // DFT matrix images -> shared memory (the global table holds 8 hi then 8 lo
+  // images): plain, hi image k0 in slot k0; split, hi image k0 in slot 2 k0 and
+  // its lo image in slot 2 k0 + 1, so that [B_hi | B_lo] is one N = 64 operand.
   {
     const uint4* src = reinterpret_cast<const uint4*>(p.dft_b);
     uint4* dst = reinterpret_cast<uint4*>(Bs);
     constexpr int per = kBImageBytes / 16;
     for (int i = tid; i < K::PLANES * NB * per; i += (int)blockDim.x) {
-      const int plane = i / (NB * per), r = i - plane * (NB * per);
-      dst[i] = __ldg(src + plane * 8 * per + r);
+      const int slot = i / per, r = i - slot * per;
+      const int plane = K::SPLIT ? (slot & 1) : 0, k0 = K::SPLIT ? (slot >> 1) : slot;
+      dst[i] = __ldg(src + (plane * 8 + k0) * per + r);
     }
   }
   if (tid == 0) {
@@ -560,6 +562,7 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
 
   const uint32_t rows_valid = (uint32_t)C << (LOG2N - 4);  // butterflies per stage
   const uint32_t idesc = make_idesc_f16(128, 32, 1, 0);
+  const uint32_t idesc64 = make_idesc_f16(128, 64, 1, 0);  // split: [B_hi | B_lo]
   const uint32_t a_base = smem_u32(A), b_base = smem_u32(Bs), raw_s = smem_u32(RAW);
   const uint32_t mbar_s = smem_u32(mbar), lbar_s = smem_u32(lbar);
   const uint32_t* raw32 = reinterpret_cast<const uint32_t*>(RAW);
@@ -635,23 +638,29 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
         tc_fence_after_sync();
         for (int t = 0; t < tiles; ++t) {
           const uint32_t a = a_base + t * kTileBytes;
-          const uint32_t d = tmem + 32u * t;
           // stage 1 with FOLD: the DFT matrix of this tile's k0
           const uint32_t kb = (K::FOLD && j == 1) ? ((uint32_t)(t * 128) >> (log2C + K::LOG2LQ)) : 0u;
-          const uint32_t bb = b_base + kb * kBImageBytes;
-          mma_f16(d, make_smem_desc(a, 4096, 1024, 2), make_smem_desc(bb, 128, 512, 0), idesc, 0);
-          mma_f16(d, make_smem_desc(a + 2048, 4096, 1024, 2),
-                  make_smem_desc(bb + 256, 128, 512, 0), idesc, 1);
-          if constexpr (SPLIT) {
-            const uint32_t alo = a + tiles * kTileBytes;
-            const uint32_t blo = bb + NB * kBImageBytes;
-            const uint32_t d2 = tmem + 32u * (tiles + t);
-            mma_f16(d2, make_smem_desc(alo, 4096, 1024, 2), make_smem_desc(bb, 128, 512, 0), idesc, 0);
-            mma_f16(d2, make_smem_desc(alo + 2048, 4096, 1024, 2),
+          if constexpr (!SPLIT) {
+            const uint32_t d = tmem + 32u * t;
+            const uint32_t bb = b_base + kb * kBImageBytes;
+            mma_f16(d, make_smem_desc(a, 4096, 1024, 2), make_smem_desc(bb, 128, 512, 0), idesc, 0);
+            mma_f16(d, make_smem_desc(a + 2048, 4096, 1024, 2),
                     make_smem_desc(bb + 256, 128, 512, 0), idesc, 1);
-            mma_f16(d2, make_smem_desc(a, 4096, 1024, 2), make_smem_desc(blo, 128, 512, 0), idesc, 1);
-            mma_f16(d2, make_smem_desc(a + 2048, 4096, 1024, 2),
-                    make_smem_desc(blo + 256, 128, 512, 0), idesc, 1);
+          } else {
+            // tile t owns TMEM columns [64 t, 64 t + 64): the main product
+            // A_hi B_hi in the first 32, the correction A_hi B_lo + A_lo B_hi in
+            // the second.  One N = 64 MMA forms A_hi [B_hi | B_lo] (the lo image
+            // follows its hi image, at the same 512-byte group stride), one
+            // N = 32 MMA adds A_lo B_hi; per K half.
+            const uint32_t dm = tmem + 64u * t;
+            const uint32_t bb = b_base + 2u * kb * kBImageBytes;
+            const uint32_t alo = a + tiles * kTileBytes;
+            mma_f16(dm, make_smem_desc(a, 4096, 1024, 2), make_smem_desc(bb, 128, 512, 0), idesc64, 0);
+            mma_f16(dm + 32u, make_smem_desc(alo, 4096, 1024, 2), make_smem_desc(bb, 128, 512, 0), idesc, 1);
+            mma_f16(dm, make_smem_desc(a + 2048, 4096, 1024, 2), make_smem_desc(bb + 256, 128, 512, 0),
+                    idesc64, 1);
+            mma_f16(dm + 32u, make_smem_desc(alo + 2048, 4096, 1024, 2),
+                    make_smem_desc(bb + 256, 128, 512, 0), idesc, 1);
           }
         }
         mma_commit(mbar_s);
@@ -671,7 +680,7 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
         // X[i] = (Re out 2i, Re out 2i+1), Y[i] = (Im out 2i, Im out 2i+1)
         float2 X[8], Y[8];
         {
-          const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + 32u * t;
+          const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (SPLIT ? 64u : 32u) * t;
           float v[32];
           tmem_ld32_wait(taddr, v);
 #pragma unroll
@@ -680,7 +689,7 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
             Y[i] = make_float2(v[16 + 2 * i], v[16 + 2 * i + 1]);
           }
           if constexpr (SPLIT) {
-            tmem_ld32_wait(taddr + 32u * tiles, v);
+            tmem_ld32_wait(taddr + 32u, v);
             const float2 s = make_float2(1.0f / 2048.0f, 1.0f / 2048.0f);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
