@@ -856,8 +856,12 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
             continue;
           }
           uint32_t* stg = reinterpret_cast<uint32_t*>(A);
-          const uint32_t key = stg_key<K>(c, kbase, log2C) << 2;
           const uint32_t base = K::OUT_C ? ((c << LOG2N) + kbase) : ((kbase << log2C) + c);
+          // bank-spreading key; for tensor-map stores the map's swizzle (the
+          // 16-byte chunk index XOR the 128-byte line index, over rows of
+          // C * 4 bytes), which is constant over a thread's 16 words here
+          const uint32_t key =
+              (!K::OUT_C && p.out_tma) ? (((base >> 5) & ((1u << (log2C - 2)) - 1u)) << 2) : (stg_key<K>(c, kbase, log2C) << 2);
           const uint32_t wstep = K::OUT_C ? kstep : (kstep << log2C);
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
@@ -909,6 +913,21 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
           *reinterpret_cast<uint4*>(o) = stg[pq];
           if constexpr (SPLIT) *reinterpret_cast<uint4*>(o + p.out_plane) = stg[nch + pq];
         }
+      } else if (p.out_tma) {
+        // tensor-map boxes of C columns x 256 elements per plane, one thread
+        if (tid == 0) {
+          const int64_t t1 = t0 & ((int64_t(1) << p.log2I1) - 1);
+          const int64_t t23 = t0 >> p.log2I1;
+          const int t2 = (int)(t23 & ((int64_t(1) << p.log2I2) - 1));
+          const int t3 = (int)(t23 >> p.log2I2);
+          const uint32_t a0 = smem_u32(A);
+          for (int pl = 0; pl < K::PLANES; ++pl)
+            for (int e0 = 0; e0 < K::N; e0 += 256)
+              tma_store_5d(&p.out_map, a0 + (uint32_t)pl * (P * 4u) + ((uint32_t)e0 << log2C) * 4u, (int)t1, e0,
+                           t2, t3, pl);
+          bulk_commit();
+          bulk_wait_read();  // the staging copy (= A) is rewritten by the next chunk
+        }
       } else {
         const int cq = log2C - 2;  // log2 of the chunks per output element index
         const uint32_t es = p.out_l.es;
@@ -932,6 +951,7 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
     __syncthreads();  // staging (= A) is rewritten by the next chunk
   }
 
+  if (!K::OUT_C && p.out_tma && tid == 0) bulk_wait_all();
   // unwind: no copy may still target this CTA's shared memory when it exits
   if (p.async_load) {
     if (K::IN_C || p.in_tma) {

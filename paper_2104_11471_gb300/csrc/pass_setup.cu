@@ -54,6 +54,63 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 }  // namespace
 
+namespace {
+// 5-D tensor map (t1, element, t2, t3, plane) of one strided side; boxes of
+// C x min(L, 256) elements; false when the layout does not fit a map
+bool encode_side_map(CUtensorMap* map, const PassParams& p, const SideLayout& l, const void* base,
+                     int64_t plane, bool f32, bool split, CUtensorMapSwizzle swz) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  const uint64_t elem = f32 ? 8 : 4;
+  const int64_t I1 = int64_t(1) << p.log2I1;
+  const bool lvl2 = p.log2I2 < 40;  // a bounded second index level
+  const int64_t I2 = lvl2 ? (int64_t(1) << p.log2I2) : 0;
+  const int64_t L = int64_t(1) << p.log2N;
+  const int64_t T = p.T;
+  // dims (innermost first): t1, element, t2, t3, plane; size-1 dims get a
+  // 16-byte stride that is never stepped
+  cuuint64_t dims[5], strides[4];
+  dims[0] = (cuuint64_t)I1;
+  dims[1] = (cuuint64_t)L;
+  strides[0] = (cuuint64_t)l.es * elem;
+  if (lvl2) {
+    dims[2] = (cuuint64_t)I2;
+    dims[3] = (cuuint64_t)(T / (I1 * I2));
+  } else {
+    dims[2] = (cuuint64_t)(T / I1);
+    dims[3] = 1;
+  }
+  strides[1] = (cuuint64_t)l.s2 * elem;
+  strides[2] = (cuuint64_t)l.s3 * elem;
+  dims[4] = (split && !f32) ? 2 : 1;
+  strides[3] = (cuuint64_t)plane * 4;
+  for (int i = 2; i <= 4; ++i)
+    if (dims[i] == 1) strides[i - 1] = 16;
+  bool ok = enc != nullptr && T % I1 == 0 && (!lvl2 || T % (I1 * I2) == 0);
+  for (int i = 0; i < 4 && ok; ++i) ok = strides[i] % 16 == 0 && strides[i] > 0 && strides[i] < (1ull << 40);
+  for (int i = 0; i < 5 && ok; ++i) ok = dims[i] >= 1 && dims[i] <= (1ull << 32);
+  const cuuint32_t box[5] = {(cuuint32_t)(1u << p.log2C), (cuuint32_t)std::min<int64_t>(L, 256), 1, 1, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  ok = ok && box[0] <= 256 && (box[0] * elem) % 16 == 0;
+  if (!ok) return false;
+  return enc(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 5,
+             const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace
+
+void encode_out_map(PassParams& p, bool split) {
+  if (!p.out_tma) return;
+  // the staging rows are C * 4 bytes; the swizzle span matches them
+  const int rowb = 4 << p.log2C;
+  const CUtensorMapSwizzle swz = rowb == 32    ? CU_TENSOR_MAP_SWIZZLE_32B
+                                 : rowb == 64  ? CU_TENSOR_MAP_SWIZZLE_64B
+                                 : rowb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                               : CU_TENSOR_MAP_SWIZZLE_NONE;
+  const bool ok = !(split && p.out_f32) && swz != CU_TENSOR_MAP_SWIZZLE_NONE && p.log2N == 8 &&
+                  encode_side_map(&p.out_map, p, p.out_l, p.out, p.out_plane, false, split, swz);
+  if (!ok) p.out_tma = 0;
+}
+
 void encode_in_map(PassParams& p, bool split) {
   if (!p.in_tma) return;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
@@ -258,6 +315,13 @@ tcfft_status geometry_try(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int6
   p.async_load = async;
   // strided input (no offset table) through tensor-map boxes when prefetching
   p.in_tma = (mode == kModeStrided && async && !in.toff && !env_int("TCFFT_NO_TMA", 0)) ? 1 : 0;
+  // strided output of a 256-point pass through tensor-map stores (rows of C * 4
+  // = 32, 64 or 128 bytes: the map's swizzle spreads the staging writes as
+  // evenly as the bank-spreading key does at this length)
+  p.out_tma = (mode != kModeContig && log2L == 8 && !out.toff && !out_scatter && C >= 8 && C <= 32 &&
+               !env_int("TCFFT_NO_TMA", 0))
+                  ? 1
+                  : 0;
   const size_t smem = padded(async ? base + raw : base);
   if (smem > 227 * 1024) return TCFFT_ERR_INVALID_SIZE;
   ps.smem = smem;

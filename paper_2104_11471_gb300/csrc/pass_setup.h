@@ -37,6 +37,9 @@ cudaError_t launch_pass(const void* fn, dim3 grid, int threads, size_t smem, cud
 // the kernel then gathers with per-thread 16-byte copies.  Call after every
 // change of p.in, p.T or p.in_plane.
 void encode_in_map(PassParams& p, bool split);
+// The same for p.out_map (strided-output two-stage passes planned with
+// p.out_tma); clears p.out_tma when the map cannot be encoded.
+void encode_out_map(PassParams& p, bool split);
 
 int ilog2(int64_t v);
 bool is_pow2(int64_t v);

@@ -355,6 +355,7 @@ tcfft_status tune_pass(tcfft_plan_s* pl, Pass& ps, int64_t L, int64_t T, int64_t
       c.p.in = reinterpret_cast<const uint32_t*>(pl->tune_buf);
       c.p.out = reinterpret_cast<uint32_t*>(pl->tune_buf);
       encode_in_map(c.p, pl->split);
+      encode_out_map(c.p, pl->split);
       void* args[1] = {&c.p};
       float ms = 0.0f;
       bool okc = true;
@@ -643,6 +644,7 @@ PassParams bound_params(const tcfft_plan_s* plan, const Pass& ps, const void* in
   p.in = bufs[ps.src] + (ps.src == BUF_WS ? ps.src_off : 0);
   p.out = bufs[ps.dst] + (ps.dst == BUF_WS ? ps.dst_off : 0);
   encode_in_map(p, plan->split);
+  encode_out_map(p, plan->split);
   return p;
 }
 
@@ -865,7 +867,9 @@ tcfft_status tcfft_exec_batch(tcfft_plan plan, const void* in, void* out, int64_
     if (ps.dst != BUF_WS) p.out_plane = per * batch;
     const dim3 grid((unsigned)std::min<int64_t>(p.nchunks, (int64_t)ps.grid.x));
     p.in_tma = ps.p.in_tma;  // re-encode for the shorter batch
+    p.out_tma = ps.p.out_tma;
     encode_in_map(p, plan->split);
+    encode_out_map(p, plan->split);
     void* args[1] = {&p};
     if (launch_pass(ps.fn, grid, ps.threads, ps.smem, s, args) != cudaSuccess) return TCFFT_ERR_LAUNCH;
   }

@@ -167,6 +167,8 @@ extern "C" tcfft_status tcfft_exec_1d_noalloc(int64_t n, int64_t batch, const vo
   ps[1].p.out = static_cast<uint32_t*>(out);
   tcfft::encode_in_map(ps[0].p, false);
   tcfft::encode_in_map(ps[1].p, false);
+  tcfft::encode_out_map(ps[0].p, false);
+  tcfft::encode_out_map(ps[1].p, false);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   for (int i = 0; i < 2; ++i) {
     void* args[1] = {&ps[i].p};
