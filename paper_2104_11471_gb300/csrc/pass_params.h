@@ -73,8 +73,8 @@ struct PassParams {
   // 16-byte cp.async gathers
   int in_tma;
   alignas(64) CUtensorMap in_map;
-  // strided output of a two-stage pass (length 256, C in {8, 16, 32}) through
-  // tensor-map stores: the staging copy is written in the map's swizzle
+  // strided output of a two-stage pass (length 256..1024, C in {8, 16, 32})
+  // through tensor-map stores: the staging copy is written in the map's swizzle
   // (16-byte chunk XOR 128-byte line, over C * 4-byte rows) and one thread
   // stores C x 256-element boxes per plane; 0 = per-thread 16-byte stores
   int out_tma;

@@ -106,7 +106,7 @@ void encode_out_map(PassParams& p, bool split) {
                                  : rowb == 64  ? CU_TENSOR_MAP_SWIZZLE_64B
                                  : rowb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
                                                : CU_TENSOR_MAP_SWIZZLE_NONE;
-  const bool ok = !(split && p.out_f32) && swz != CU_TENSOR_MAP_SWIZZLE_NONE && p.log2N == 8 &&
+  const bool ok = !(split && p.out_f32) && swz != CU_TENSOR_MAP_SWIZZLE_NONE && p.log2N >= 8 &&
                   encode_side_map(&p.out_map, p, p.out_l, p.out, p.out_plane, false, split, swz);
   if (!ok) p.out_tma = 0;
 }
@@ -315,11 +315,12 @@ tcfft_status geometry_try(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int6
   p.async_load = async;
   // strided input (no offset table) through tensor-map boxes when prefetching
   p.in_tma = (mode == kModeStrided && async && !in.toff && !env_int("TCFFT_NO_TMA", 0)) ? 1 : 0;
-  // strided output of a 256-point pass through tensor-map stores (rows of C * 4
-  // = 32, 64 or 128 bytes: the map's swizzle spreads the staging writes as
-  // evenly as the bank-spreading key does at this length)
-  p.out_tma = (mode != kModeContig && log2L == 8 && !out.toff && !out_scatter && C >= 8 && C <= 32 &&
-               !env_int("TCFFT_NO_TMA", 0))
+  // strided output of a two-stage pass through tensor-map stores (rows of
+  // C * 4 = 32, 64 or 128 bytes in the map's swizzle).  Measured at 2^28
+  // points: 256-point passes 9-13 % faster, 512 13 %, 1024 6 %; at 2048 the
+  // swizzle's staging bank conflicts outweigh the saved stores (19 % slower).
+  p.out_tma = (mode != kModeContig && log2L >= 8 && log2L <= env_int("TCFFT_TMA_STORE_MAX_LOG2", 10) &&
+               !out.toff && !out_scatter && C >= 8 && C <= 32 && !env_int("TCFFT_NO_TMA", 0))
                   ? 1
                   : 0;
   const size_t smem = padded(async ? base + raw : base);
