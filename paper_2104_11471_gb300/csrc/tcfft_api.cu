@@ -412,7 +412,8 @@ constexpr int64_t kNoLevel = int64_t(1) << 40;  // "unbounded" index level
 
 tcfft_status plan_1d(tcfft_plan_s* pl) {
   const int64_t n = pl->n, B = pl->batch;
-  const int64_t single = pl->split ? kSingleSplit : kSinglePlain;
+  const int64_t single = std::min<int64_t>(pl->split ? kSingleSplit : kSinglePlain,
+                                           int64_t(1) << env_int("TCFFT_SINGLE_MAX_LOG2", 14));  // tuning override
   if (n <= single) {
     Side s{n, 0, 0, 1};
     return add_pass(pl, n, B, kNoLevel, 1, s, s, BUF_IN, BUF_OUT, 0, 0);
@@ -423,17 +424,22 @@ tcfft_status plan_1d(tcfft_plan_s* pl) {
     pl->ws = nullptr;
     return TCFFT_ERR_ALLOC;
   }
-  // three passes from 2^24 (tuning override TCFFT_THREE_PASS_MIN), always
+  // three passes from 2^22 (tuning override TCFFT_THREE_PASS_MIN), always
   // beyond 2^24, and for split precision beyond 2^22 (the four-step split
-  // would need strided passes longer than the split kernels' 2^11)
-  const bool three = lg >= env_int("TCFFT_THREE_PASS_MIN", 24) || lg > 24 || (pl->split && lg > 22);
+  // would need strided passes longer than the split kernels' 2^11).  Measured
+  // at 2^28 points: 2^22 as 16 x 512 x 512 1.53 ms (2048 x 2048: 1.92 ms,
+  // 64 x 256 x 256: 1.62 ms); 2^23 as 128 x 256 x 256 1.61 ms (two passes:
+  // 2.65 ms); 2^24 as 256^3 1.45 ms (16 x 1024 x 1024: 1.75 ms).
+  const bool three = lg >= env_int("TCFFT_THREE_PASS_MIN", 22) || lg > 24 || (pl->split && lg > 22);
   if (three) {
     // n = N1 N2 N3 (M = N2 N3) in three passes of short transforms, so that
     // every pass keeps small per-CTA tiles with prefetch:
     //  A: N1-point DFTs of the columns x[M n1 + m], times W_n^{m k1} -> ws
     //  B: N2-point DFTs of ws[k1 M + N3 n2 + n3], times W_M^{n3 k2}, in place
     //  C: N3-point DFTs of ws rows (k1, k2) -> X[k1 + N1 k2 + N1 N2 k3]
-    const int l1 = 8, l2 = (lg - 8 + 1) / 2, l3 = lg - 8 - l2;
+    const int l1_default = lg == 22 ? 4 : (lg == 23 ? 7 : 8);
+    const int l1 = std::max(4, std::min(8, env_int("TCFFT_THREE_PASS_L1", l1_default)));  // tuning override
+    const int l2 = (lg - l1 + 1) / 2, l3 = lg - l1 - l2;
     const int64_t N1 = int64_t(1) << l1, N2 = int64_t(1) << l2, N3 = int64_t(1) << l3, M = N2 * N3;
     Side a{1, n, 0, M};
     tcfft_status st = add_pass(pl, N1, B * M, M, kNoLevel, a, a, BUF_IN, BUF_WS, 1, lg);
@@ -444,7 +450,8 @@ tcfft_status plan_1d(tcfft_plan_s* pl) {
     Side cin{M, N3, n, 1}, cout{1, N1, n, N1 * N2};
     return add_pass(pl, N3, B * N1 * N2, N1, N2, cin, cout, BUF_WS, BUF_OUT, 0, 0);
   }
-  const int64_t N1 = int64_t(1) << ((lg + 1) / 2), N2 = n / N1;
+  const int l1 = env_int("TCFFT_FOUR_STEP_L1", (lg + 1) / 2);  // tuning override
+  const int64_t N1 = int64_t(1) << l1, N2 = n / N1;
   // pass 1: columns n2 of length N1 (stride N2), times W_n^{n2 k1}
   Side c1{1, n, 0, N2};
   tcfft_status st = add_pass(pl, N1, B * N2, N2, kNoLevel, c1, c1, BUF_IN, BUF_WS, 1, lg);
