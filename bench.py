@@ -486,7 +486,8 @@ def run_serve(args, world, rank, local):
                    "parallelism": f"replicas x{world}"},
         "serve": {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
                   "requests": st["requests"], "batches": st["batches"], "peak_hbm_bytes": st["peak_hbm_bytes"],
-                  "plain": st.get("plain"), "split": st.get("split")},
+                  "plain": st.get("plain"), "split": st.get("split"),
+                  "by_size": {k: st[k] for k in ("small_points", "medium_points", "large_points") if k in st}},
         "roofline": {"bound": "hbm", "achieved": round(alg / span / 1e9, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(alg / span / 1e9 / peak, 4), "traffic": None,
                      "kernel": "pass_kernel (offered load, not saturating)", "peak_kind": peak_kind},

@@ -84,6 +84,10 @@ typedef enum {
 #define TCFFT_PLAN_SCALE 8u    /* multiply the results by 1/N (N = points of one
                                   transform); with TCFFT_PLAN_INVERSE the exact
                                   inverse of the forward transform */
+#define TCFFT_PLAN_SHARE_SM 16u /* use at most half of each SM's CTA slots, so
+                                  that kernels on other (higher-priority)
+                                  streams find room while this plan runs
+                                  (serving: large jobs beside small ones) */
 
 /* Plan a batch of `batch` 1D transforms of length n (the paper's
  * tcfftPlan1D(plan, nx, batch), Sec. 3.1).  Allocates device twiddle tables

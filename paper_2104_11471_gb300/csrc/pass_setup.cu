@@ -179,7 +179,7 @@ namespace {
 // One candidate geometry: `threads` per CTA (256 or 128), prefetching the next
 // chunk into a raw buffer (async = 1) or loading synchronously (async = 0).
 tcfft_status geometry_try(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int64_t I2, Side in, Side out,
-                          bool split, int64_t target_points, int threads, int async) {
+                          bool split, int64_t target_points, int threads, int async, bool share_sm) {
 
   std::memset(&ps.p, 0, sizeof(ps.p));
   PassParams& p = ps.p;
@@ -330,6 +330,7 @@ tcfft_status geometry_try(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int6
   if (occ < 1) return TCFFT_ERR_INVALID_SIZE;
   const int occ_env = env_int("TCFFT_CTAS_PER_SM", 0);  // tuning override
   if (occ_env > 0) occ = std::min(occ, occ_env);
+  if (share_sm) occ = std::max(1, occ / 2);  // leave room for other streams' kernels
   ps.grid = dim3((unsigned)std::min<int64_t>(p.nchunks, (int64_t)occ * sms));
   ps.occ = occ;
   ps.regs = fa0.numRegs;
@@ -338,7 +339,8 @@ tcfft_status geometry_try(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int6
 }  // namespace
 
 tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int64_t I2, Side in,
-                           Side out, bool split, int64_t target_points, int force_threads, int force_async) {
+                           Side out, bool split, int64_t target_points, int force_threads, int force_async,
+                           bool share_sm) {
   // The pass is latency-bound (each CTA runs a serial chain per chunk: load,
   // then per stage MMA issue, MMA completion, TMEM loads, epilogue, barrier):
   // pick the candidate with the most resident CTAs per SM (independent
@@ -359,7 +361,7 @@ tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int
       if (as && sync_env) continue;
       if (!as && force_async == 1) continue;
       PassLaunch c = ps;
-      const tcfft_status st = geometry_try(c, L, T, I1, I2, in, out, split, target_points, thr, as);
+      const tcfft_status st = geometry_try(c, L, T, I1, I2, in, out, split, target_points, thr, as, share_sm);
       if (st != TCFFT_OK) {
         last = st;
         continue;

@@ -59,6 +59,6 @@ const void* pass_fn(int log2N, int mode, bool split);
 // the load mode instead of the planner's choice.
 tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int64_t I2, Side in,
                            Side out, bool split, int64_t target_points = 0, int force_threads = 0,
-                           int force_async = -1);
+                           int force_async = -1, bool share_sm = false);
 
 }  // namespace tcfft

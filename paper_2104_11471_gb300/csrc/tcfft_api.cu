@@ -82,7 +82,8 @@ struct tcfft_plan_s {
   int dims = 1;
   int64_t n = 0, nx = 0, ny = 0, batch = 0;
   bool split = false;
-  bool fp32 = false;  // TCFFT_FP32: user buffers are interleaved FP32 complex (split kernels inside)
+  bool fp32 = false;
+  bool share_sm = false;  // TCFFT_PLAN_SHARE_SM  // TCFFT_FP32: user buffers are interleaved FP32 complex (split kernels inside)
   int64_t points = 0;  // total complex points per plane
   std::vector<Pass> passes;
   std::map<int, TwTable> tables;
@@ -207,7 +208,7 @@ tcfft_status add_pass(tcfft_plan_s* pl, int64_t L, int64_t T, int64_t I1, int64_
                       Side out, Buf src, Buf dst, int otw_level, int log2M, int group = 0,
                       int64_t src_off = 0, int64_t dst_off = 0) {
   Pass ps;
-  tcfft_status st = pass_geometry(ps, L, T, I1, I2, in, out, pl->split);
+  tcfft_status st = pass_geometry(ps, L, T, I1, I2, in, out, pl->split, 0, 0, -1, pl->share_sm);
   if (st != TCFFT_OK) return st;
   ps.src = src;
   ps.dst = dst;
@@ -306,8 +307,8 @@ tcfft_status tune_pass(tcfft_plan_s* pl, Pass& ps, int64_t L, int64_t T, int64_t
                        Side out, int otw_level, int log2M) {
   const int mode = (in.es == 1) ? ((out.es == 1) ? 0 : 2) : 1;
   char key[128];
-  std::snprintf(key, sizeof(key), "v3_L%d_m%d_s%d_T%d_g%d", ilog2(L), mode, pl->split ? 1 : 0, ilog2(T),
-                (in.toff || out.toff) ? 1 : 0);
+  std::snprintf(key, sizeof(key), "v3_L%d_m%d_s%d_T%d_g%d_h%d", ilog2(L), mode, pl->split ? 1 : 0, ilog2(T),
+                (in.toff || out.toff) ? 1 : 0, pl->share_sm ? 1 : 0);
   std::lock_guard<std::mutex> lock(g_tune_mu);
   tune_load();
   auto it = g_tune_cache.find(key);
@@ -347,7 +348,7 @@ tcfft_status tune_pass(tcfft_plan_s* pl, Pass& ps, int64_t L, int64_t T, int64_t
     for (int64_t cand : cands) {
       Pass c;
       if (pass_geometry(c, L, T, I1, I2, in, out, pl->split, cand & 0xFFFFF, (int)((cand >> 20) & 1023),
-                        (int)((cand >> 30) & 3) - 1) != TCFFT_OK)
+                        (int)((cand >> 30) & 3) - 1, pl->share_sm) != TCFFT_OK)
         continue;
       c.src = ps.src;
       c.dst = ps.dst;
@@ -381,7 +382,7 @@ tcfft_status tune_pass(tcfft_plan_s* pl, Pass& ps, int64_t L, int64_t T, int64_t
   }
   Pass c;
   if (pass_geometry(c, L, T, I1, I2, in, out, pl->split, best & 0xFFFFF, (int)((best >> 20) & 1023),
-                    (int)((best >> 30) & 3) - 1) != TCFFT_OK)
+                    (int)((best >> 30) & 3) - 1, pl->share_sm) != TCFFT_OK)
     return TCFFT_OK;
   const PassParams keep = ps.p;
   ps.fn = c.fn;
@@ -558,13 +559,15 @@ tcfft_status plan_many(tcfft_plan_s* pl, int64_t count, const int64_t* n0, const
   return TCFFT_OK;
 }
 
-constexpr unsigned kPlanFlags = TCFFT_PLAN_AUTOTUNE | TCFFT_PLAN_GRAPH | TCFFT_PLAN_INVERSE | TCFFT_PLAN_SCALE;
+constexpr unsigned kPlanFlags =
+    TCFFT_PLAN_AUTOTUNE | TCFFT_PLAN_GRAPH | TCFFT_PLAN_INVERSE | TCFFT_PLAN_SCALE | TCFFT_PLAN_SHARE_SM;
 
 void apply_flags(tcfft_plan_s* pl, unsigned flags) {
   pl->autotune = (flags & TCFFT_PLAN_AUTOTUNE) || env_int("TCFFT_AUTOTUNE", 0);
   pl->use_graph = (flags & TCFFT_PLAN_GRAPH) != 0;
   pl->inverse = (flags & TCFFT_PLAN_INVERSE) != 0;
   pl->normalise = (flags & TCFFT_PLAN_SCALE) != 0;
+  pl->share_sm = (flags & TCFFT_PLAN_SHARE_SM) != 0;
 }
 
 // Direction and scaling: the inverse DFT is conj(DFT(conj(x))), so the first

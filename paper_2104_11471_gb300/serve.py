@@ -13,6 +13,10 @@ device.  A scheduling loop on the host:
   (device-to-device copies) and runs the plan on that batch with
   tcfft_exec_batch -- so requests that arrive while others run on the GPU
   join the next batch and their work overlaps on the device;
+* keeps small jobs (at most `small_points` points) off the queues of large
+  ones: they run on their own high-priority streams, and every plan leaves
+  half of each SM's CTA slots free (TCFFT_PLAN_SHARE_SM), so a small job
+  does not wait for a large job's persistent grid to drain;
 * retires finished batches (CUDA events), releasing their memory.
 
 Latency is arrival to completion as seen by the host.  All transform work
@@ -27,7 +31,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import TCFFT_FP16, TCFFT_FP16_SPLIT, Plan
+from . import TCFFT_FP16, TCFFT_FP16_SPLIT, TCFFT_PLAN_SHARE_SM, Plan
 
 
 @dataclass
@@ -85,11 +89,18 @@ def poisson_trace(rate: float = 2000.0, seconds: float = 10.0, seed: int = 5, ma
 
 class FFTServer:
     def __init__(self, hbm_budget: int = 16 << 30, slots: int = 4, depth: int = 2,
-                 job_points: int = 1 << 26, pool_points: int = 1 << 28, seed: int = 5):
+                 job_points: int = 1 << 26, pool_points: int = 1 << 28, seed: int = 5,
+                 small_slots: int = 3, small_points: int = 1 << 22, share_sm: bool = True):
         import torch
         self.torch = torch
         self.budget = hbm_budget
+        # streams 0..slots-1 take large jobs; the high-priority rest small ones
         self.slots = [torch.cuda.Stream() for _ in range(slots)]
+        self.n_large = slots
+        hi_prio = torch.cuda.Stream.priority_range()[1] if hasattr(torch.cuda.Stream, "priority_range") else -1
+        self.slots += [torch.cuda.Stream(priority=hi_prio) for _ in range(small_slots)]
+        self.small_points = small_points
+        self.share_sm = share_sm
         self.depth = depth                # batches in flight per stream
         self.job_points = job_points      # merge requests up to this many points
         self.plans = {}
@@ -116,8 +127,9 @@ class FFTServer:
         if p is None:
             prec = TCFFT_FP16_SPLIT if split else TCFFT_FP16
             cap = self.capacity(shape)
-            p = (Plan.plan_1d(shape[0], cap, prec) if len(shape) == 1
-                 else Plan.plan_2d(shape[0], shape[1], cap, prec))
+            flags = TCFFT_PLAN_SHARE_SM if self.share_sm else 0
+            p = (Plan.plan_1d(shape[0], cap, prec, flags) if len(shape) == 1
+                 else Plan.plan_2d(shape[0], shape[1], cap, prec, flags))
             self.plans[key] = p
         return p
 
@@ -191,33 +203,56 @@ class FFTServer:
                     per_slot[job.stream_idx] -= 1
                     inflight.remove(job)
             launched = False
-            while queue:
-                free = [i for i, c in enumerate(per_slot) if c < self.depth]
-                if not free:
-                    break
-                head = queue[0]
-                key = (head.shape, head.split)
-                cap = self.capacity(head.shape)
-                group, total = [], 0
-                for r in queue:
-                    if (r.shape, r.split) == key and total + r.batch <= cap:
-                        group.append(r)
-                        total += r.batch
-                planes = 2 if head.split else 1
-                nbytes = 2 * planes * total * int(np.prod(head.shape)) * 4
-                if self.in_use + nbytes > self.budget:
-                    if not inflight:
-                        raise RuntimeError("request larger than the HBM budget")
-                    break  # admission: wait until running batches free memory
-                for r in group:
-                    queue.remove(r)
-                sidx = min(free, key=lambda i: per_slot[i])
-                inflight.append(self._launch(group, key, sidx))
-                per_slot[sidx] += 1
-                self.in_use += nbytes
-                self.peak_in_use = max(self.peak_in_use, self.in_use)
-                batches += 1
-                launched = True
+            # start every job that has room: scan the queue in arrival order,
+            # one group per (shape, precision); small and large jobs use their
+            # own streams, and a pool that cannot start its oldest job stays
+            # closed for this scan (arrival order within each pool)
+            blocked = set()
+            progressed = True
+            while queue and progressed:
+                progressed = False
+                seen = set()
+                for head in list(queue):
+                    key = (head.shape, head.split)
+                    if key in seen:
+                        continue
+                    seen.add(key)
+                    cap = self.capacity(head.shape)
+                    group, total = [], 0
+                    for r in queue:
+                        if (r.shape, r.split) == key and total + r.batch <= cap:
+                            group.append(r)
+                            total += r.batch
+                    pts = total * int(np.prod(head.shape))
+                    pool = "small" if pts <= self.small_points else "large"
+                    if pool in blocked:
+                        continue
+                    if pool == "small":
+                        free = [i for i in range(self.n_large, len(self.slots)) if per_slot[i] < self.depth]
+                        free = free or [i for i in range(self.n_large) if per_slot[i] == 0]
+                    else:
+                        free = [i for i in range(self.n_large) if per_slot[i] < self.depth]
+                    if not free:
+                        blocked.add(pool)
+                        continue
+                    planes = 2 if head.split else 1
+                    nbytes = 2 * planes * pts * 4
+                    if self.in_use + nbytes > self.budget:
+                        if not inflight:
+                            raise RuntimeError("request larger than the HBM budget")
+                        blocked.add(pool)  # admission: wait until running batches free memory
+                        continue
+                    for r in group:
+                        queue.remove(r)
+                    sidx = min(free, key=lambda i: per_slot[i])
+                    inflight.append(self._launch(group, key, sidx))
+                    per_slot[sidx] += 1
+                    self.in_use += nbytes
+                    self.peak_in_use = max(self.peak_in_use, self.in_use)
+                    batches += 1
+                    launched = True
+                    progressed = True
+                    break  # the queue changed: scan again from its head
             if not launched and not (pending and pending[0].t_arrival <= time.perf_counter() - t0):
                 time.sleep(20e-6)
         torch.cuda.synchronize()
@@ -231,6 +266,13 @@ class FFTServer:
                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                "mean_ms": float(lat.mean() * 1e3), "gflops": flops / span / 1e9, "span_s": span,
                "peak_hbm_bytes": self.peak_in_use}
+        # by request size: small requests stuck behind large ones show here
+        for name, lo, hi in (("small", 0, 1 << 20), ("medium", 1 << 20, 1 << 24), ("large", 1 << 24, 1 << 62)):
+            sel = [r for r in requests if lo <= r.points < hi]
+            if sel:
+                la = np.array([r.t_done - r.t_arrival for r in sel])
+                out[f"{name}_points"] = {"requests": len(sel), "p50_ms": float(np.percentile(la, 50) * 1e3),
+                                         "p99_ms": float(np.percentile(la, 99) * 1e3)}
         for split in (False, True):
             sel = [r for r in requests if r.split == split]
             if sel:
