@@ -470,14 +470,19 @@ tcfft_status plan_2d(tcfft_plan_s* pl) {
   tcfft_status st = add_pass(pl, ny, B * nx, kNoLevel, 1, r, r, BUF_IN, BUF_OUT, 0, 0);
   if (st != TCFFT_OK) return st;
   const int64_t cap = pl->split ? kCapSplit : kCapPlain;
-  if (8 * nx <= cap) {
+  // one column pass up to 2048 rows; longer columns in two passes, 16 x nx/16
+  // (measured at 2^28 points: 4096^2 plain 2.27 -> 1.48 ms, split 3.81 ->
+  // 2.97 ms; 8192^2 plain 1.91 -> 1.64 ms against 128 x 64, split 4.88 -> 3.70;
+  // 1024^2 keeps its single pass, 1.16 ms against 1.61 ms for 16 x 64)
+  const int col_max = env_int("TCFFT_2D_COL_MAX_LOG2", 11);  // tuning override
+  if (8 * nx <= cap && ilog2(nx) <= col_max) {
     // columns: ny * B transforms of length nx, stride ny, in place on out
     Side c{1, mat, 0, ny};
     return add_pass(pl, nx, B * ny, ny, kNoLevel, c, c, BUF_OUT, BUF_OUT, 0, 0);
   }
   // columns too long for one CTA group: nx = N1 N2 in two passes
   const int lg = ilog2(nx);
-  const int64_t N1 = int64_t(1) << ((lg + 1) / 2), N2 = nx / N1;
+  const int64_t N1 = int64_t(1) << env_int("TCFFT_2D_COL_L1", 4), N2 = nx / N1;  // tuning override
   pl->ws_bytes = (size_t)B * mat * 4 * (pl->split ? 2 : 1);
   if (cudaMalloc(&pl->ws, pl->ws_bytes) != cudaSuccess) {
     pl->ws = nullptr;
