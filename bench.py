@@ -443,7 +443,7 @@ def build_ragged(args, dev, rank):
         return {"ms_per_step": round(ms, 4), "gflops": round(flops / (ms / 1e3) / 1e9, 1),
                 "launches_per_step": launches}
     cpu_sizes = [sh for sh in shapes[:64]]
-    return entries, cfg, cpu_sizes, (h, lo), per_size_launches
+    return entries, cfg, cpu_sizes, (h, None), per_size_launches
 
 
 def run_serve(args, world, rank, local):
