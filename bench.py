@@ -63,9 +63,12 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
+        import tempfile
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        # raw samples: $TCFFT_CLOCKS_DIR/clocks_gpu<i>.csv when set, else a temporary file
+        d = os.environ.get("TCFFT_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"clocks_gpu{gpu_index}.csv")
 
     def start(self):
         try:

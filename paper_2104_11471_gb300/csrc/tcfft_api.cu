@@ -585,9 +585,6 @@ void apply_direction(tcfft_plan_s* pl) {
   while (i < pl->passes.size()) {
     size_t j = i;
     while (j + 1 < pl->passes.size() && pl->passes[j + 1].group == pl->passes[i].group) ++j;
-    int64_t n = 1;  // transform size of the group: product of its pass lengths
-    for (size_t k = i; k <= j; ++k) n *= int64_t(1) << pl->passes[k].p.log2N;
-    if (pl->dims == 2) n = pl->nx * pl->ny;
     pl->passes[i].p.conj_in = pl->inverse ? 1 : 0;
     pl->passes[j].p.conj_out = pl->inverse ? 1 : 0;
     // 1/N is spread over the transform: every radix-16 stage uses F_16 / 16
@@ -595,7 +592,6 @@ void apply_direction(tcfft_plan_s* pl) {
     // radix-R step scales by 1/R, so intermediates keep the input's magnitude
     if (pl->normalise)
       for (size_t k = i; k <= j; ++k) pl->passes[k].p.prescale = 1.0f / (float)(1 << (pl->passes[k].p.log2N % 4));
-    (void)n;
     i = j + 1;
   }
 }
