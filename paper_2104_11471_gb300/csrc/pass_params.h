@@ -72,13 +72,13 @@ struct PassParams {
   // elements), encoded at exec time for the bound pointer; 0 = per-thread
   // 16-byte cp.async gathers
   int in_tma;
-  alignas(64) CUtensorMap in_map;
+  CUtensorMap in_map;  // 128-byte aligned by its type
   // strided output of a two-stage pass (length 256..1024, C in {8, 16, 32})
   // through tensor-map stores: the staging copy is written in the map's swizzle
   // (16-byte chunk XOR 128-byte line, over C * 4-byte rows) and one thread
   // stores C x 256-element boxes per plane; 0 = per-thread 16-byte stores
   int out_tma;
-  alignas(64) CUtensorMap out_map;
+  CUtensorMap out_map;
   int in_gather;          // contiguous input, one offset per transform (see SideLayout)
   int out_scatter;        // contiguous output, one offset per transform
   int async_load;         // 1: prefetch the next chunk with cp.async into a raw buffer
