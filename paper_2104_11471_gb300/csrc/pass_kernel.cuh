@@ -860,8 +860,12 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
           // bank-spreading key; for tensor-map stores the map's swizzle (the
           // 16-byte chunk index XOR the 128-byte line index, over rows of
           // C * 4 bytes), which is constant over a thread's 16 words here
-          const uint32_t key =
-              (!K::OUT_C && p.out_tma) ? (((base >> 5) & ((1u << (log2C - 2)) - 1u)) << 2) : (stg_key<K>(c, kbase, log2C) << 2);
+          uint32_t key = stg_key<K>(c, kbase, log2C) << 2;
+          if constexpr (K::OUT_C) {
+            if (K::S == 3 && p.out_tma) key = ((base >> 5) & 7u) << 2;  // rows of 32 points
+          } else {
+            if (p.out_tma) key = ((base >> 5) & ((1u << (log2C - 2)) - 1u)) << 2;
+          }
           const uint32_t wstep = K::OUT_C ? kstep : (kstep << log2C);
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
@@ -895,7 +899,19 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
     if constexpr (!K::DIRECT_OUT) {
       const uint4* stg = reinterpret_cast<const uint4*>(A);
       const uint32_t nch = P >> 2;
-      if constexpr (K::OUT_C) {
+      if (K::OUT_C && K::S == 3 && p.out_tma) {
+        // rows of 32 points in the 128-byte swizzle, up to 256 rows per box;
+        // rows past the end of the output are not written
+        if (tid == 0) {
+          const int row0 = (int)((gout - p.out) >> 5);
+          const uint32_t a0 = smem_u32(A);
+          for (int pl = 0; pl < K::PLANES; ++pl)
+            for (uint32_t r0 = 0; r0 < (P >> 5); r0 += 256)
+              tma_store_5d(&p.out_map, a0 + (uint32_t)pl * (P * 4u) + r0 * 128u, 0, row0 + (int)r0, pl, 0, 0);
+          bulk_commit();
+          bulk_wait_read();  // the staging copy (= A) is rewritten by the next chunk
+        }
+      } else if constexpr (K::OUT_C) {
         const uint32_t vchunks = ((uint32_t)nvalid << LOG2N) >> 2;
         for (uint32_t q = tid; q < vchunks; q += blockDim.x) {
           const uint32_t c = (q << 2) >> LOG2N;
@@ -951,7 +967,7 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
     __syncthreads();  // staging (= A) is rewritten by the next chunk
   }
 
-  if (!K::OUT_C && p.out_tma && tid == 0) bulk_wait_all();
+  if (p.out_tma && tid == 0) bulk_wait_all();
   // unwind: no copy may still target this CTA's shared memory when it exits
   if (p.async_load) {
     if (K::IN_C || p.in_tma) {

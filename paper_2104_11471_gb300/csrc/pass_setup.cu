@@ -100,6 +100,25 @@ bool encode_side_map(CUtensorMap* map, const PassParams& p, const SideLayout& l,
 
 void encode_out_map(PassParams& p, bool split) {
   if (!p.out_tma) return;
+  if (p.out_l.es == 1) {
+    // contiguous output: the output buffer as rows of 32 points (128 bytes) in
+    // the 128-byte swizzle; boxes of up to 256 rows per plane
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    const uint64_t points = (uint64_t)p.T << p.log2N;
+    const uint64_t P = (uint64_t)1 << (p.log2C + p.log2N);
+    const cuuint64_t dims[5] = {32, points / 32, (cuuint64_t)(split ? 2 : 1), 1, 1};
+    const cuuint64_t strides[4] = {128, split ? (cuuint64_t)p.out_plane * 4 : 16, 16, 16};
+    const cuuint32_t box[5] = {32, (cuuint32_t)std::min<uint64_t>(P / 32, 256), 1, 1, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const bool ok = enc != nullptr && !(split && p.out_f32) && points % 32 == 0 && P % 32 == 0 &&
+                    points / 32 < (1ull << 31) &&  // row coordinates are 32-bit
+                    strides[1] % 16 == 0 && strides[1] < (1ull << 40) &&
+                    enc(&p.out_map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 5, p.out, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    if (!ok) p.out_tma = 0;
+    return;
+  }
   // the staging rows are C * 4 bytes; the swizzle span matches them
   const int rowb = 4 << p.log2C;
   const CUtensorMapSwizzle swz = rowb == 32    ? CU_TENSOR_MAP_SWIZZLE_32B
@@ -323,6 +342,11 @@ tcfft_status geometry_try(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int6
                !out.toff && !out_scatter && C >= 8 && C <= 32 && !env_int("TCFFT_NO_TMA", 0))
                   ? 1
                   : 0;
+  // contiguous output of a three-stage pass (N >= 4096): the staging key is the
+  // 128-byte swizzle there, so the chunk leaves through tensor-map stores too
+  if (mode == kModeContig && log2L >= 12 && !out.toff && !out_scatter && !env_int("TCFFT_NO_TMA", 0) &&
+      !env_int("TCFFT_NO_TMA_CONTIG_STORE", 0))
+    p.out_tma = 1;
   const size_t smem = padded(async ? base + raw : base);
   if (smem > 227 * 1024) return TCFFT_ERR_INVALID_SIZE;
   ps.smem = smem;
