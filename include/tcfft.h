@@ -134,10 +134,15 @@ tcfft_status tcfft_exec(tcfft_plan plan, const void* in, void* out, void* stream
 tcfft_status tcfft_exec_batch(tcfft_plan plan, const void* in, void* out, int64_t batch, void* stream);
 
 /* End-to-end variant for host buffers: copies host_in to a plan-owned
- * device buffer, runs tcfft_exec, copies the result to host_out, all on
- * `stream`, and synchronises the stream before returning.  host_in and
- * host_out hold tcfft_io_bytes(plan) bytes each (pinned memory gives full
- * copy bandwidth).  The device buffers are allocated on the first call. */
+ * device buffer, runs the plan, copies the result to host_out, and returns
+ * once the result is in host_out.  host_in and host_out hold
+ * tcfft_io_bytes(plan) bytes each (pinned memory gives full copy bandwidth
+ * and the overlap below).  Batches of one plane (TCFFT_FP16, TCFFT_FP32) of
+ * at least 2^22 points run as up to 8 slices of whole transforms whose
+ * uploads, transforms (on `stream`) and downloads overlap, on two streams
+ * the plan owns; other plans copy, run and copy back on `stream`.  The
+ * result equals tcfft_exec's bit for bit.  The device buffers and streams
+ * are allocated on the first call. */
 tcfft_status tcfft_exec_host(tcfft_plan plan, const void* host_in, void* host_out, void* stream);
 
 /* Frees everything the plan owns.  NULL is accepted. */

@@ -78,12 +78,14 @@ tcfft_status from_cuda(cudaError_t e) {
 
 }  // namespace
 
+constexpr int kHostSlices = 8;  // tcfft_exec_host: batch slices in flight
+
 struct tcfft_plan_s {
   int dims = 1;
   int64_t n = 0, nx = 0, ny = 0, batch = 0;
   bool split = false;
-  bool fp32 = false;
-  bool share_sm = false;  // TCFFT_PLAN_SHARE_SM  // TCFFT_FP32: user buffers are interleaved FP32 complex (split kernels inside)
+  bool fp32 = false;      // TCFFT_FP32: user buffers are interleaved FP32 complex (split kernels inside)
+  bool share_sm = false;  // TCFFT_PLAN_SHARE_SM
   int64_t points = 0;  // total complex points per plane
   std::vector<Pass> passes;
   std::map<int, TwTable> tables;
@@ -93,6 +95,10 @@ struct tcfft_plan_s {
   size_t ws_bytes = 0;
   void* h_in_dev = nullptr;
   void* h_out_dev = nullptr;
+  // tcfft_exec_host pipeline: upload and download streams, one event pair per slice
+  cudaStream_t h_up = nullptr, h_down = nullptr;
+  cudaEvent_t h_entry = nullptr;
+  cudaEvent_t h_ev_up[kHostSlices] = {}, h_ev_done[kHostSlices] = {};
   size_t table_bytes = 0;
   bool autotune = false;              // time candidate geometries at plan time
   bool inverse = false;               // sign + (TCFFT_PLAN_INVERSE)
@@ -117,6 +123,13 @@ struct tcfft_plan_s {
     cudaFree(ws);
     cudaFree(h_in_dev);
     cudaFree(h_out_dev);
+    if (h_up) cudaStreamDestroy(h_up);
+    if (h_down) cudaStreamDestroy(h_down);
+    if (h_entry) cudaEventDestroy(h_entry);
+    for (int i = 0; i < kHostSlices; ++i) {
+      if (h_ev_up[i]) cudaEventDestroy(h_ev_up[i]);
+      if (h_ev_done[i]) cudaEventDestroy(h_ev_done[i]);
+    }
   }
 
   size_t io_bytes() const { return (size_t)points * 4u * (split ? 2u : 1u); }
@@ -903,14 +916,67 @@ tcfft_status tcfft_exec_host(tcfft_plan plan, const void* host_in, void* host_ou
     }
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpyAsync(plan->h_in_dev, host_in, bytes, cudaMemcpyHostToDevice, s);
+  // Single-plane batches (plain or FP32) run as up to kHostSlices slices of
+  // whole transforms: slice j's upload (upload stream), transform (the
+  // caller's stream, so that slices share the workspace in turn) and download
+  // (download stream) are chained by events, so uploads, transforms and
+  // downloads of different slices overlap on the copy engines and the SMs.
+  int slices = 1;
+  if (plan->dims != 0 && (!plan->split || plan->fp32) && plan->batch >= 2 && plan->points >= (int64_t(1) << 22)) {
+    while (slices < kHostSlices && plan->batch % (2 * slices) == 0 &&
+           plan->points / (2 * slices) >= (int64_t(1) << 21))
+      slices *= 2;
+  }
+  if (slices > 1 && !plan->h_up) {
+    bool ok = cudaStreamCreateWithFlags(&plan->h_up, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&plan->h_down, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&plan->h_entry, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < kHostSlices && ok; ++i)
+      ok = cudaEventCreateWithFlags(&plan->h_ev_up[i], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&plan->h_ev_done[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) slices = 1;  // the handles made so far are released with the plan
+  }
+  if (slices == 1 || !plan->h_up) {
+    cudaError_t e = cudaMemcpyAsync(plan->h_in_dev, host_in, bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    tcfft_status st = tcfft_exec(plan, plan->h_in_dev, plan->h_out_dev, stream);
+    if (st != TCFFT_OK) return st;
+    e = cudaMemcpyAsync(host_out, plan->h_out_dev, bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    return from_cuda(cudaStreamSynchronize(s));
+  }
+  const int64_t per_slice = plan->batch / slices;
+  const size_t sbytes = bytes / (size_t)slices;
+  const char* hin = static_cast<const char*>(host_in);
+  char* hout = static_cast<char*>(host_out);
+  char* din = static_cast<char*>(plan->h_in_dev);
+  char* dout = static_cast<char*>(plan->h_out_dev);
+  // the slices start after the caller's earlier work on `stream`
+  cudaError_t e = cudaEventRecord(plan->h_entry, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->h_up, plan->h_entry, 0);
+  for (int j = 0; j < slices && e == cudaSuccess; ++j) {
+    const size_t off = (size_t)j * sbytes;
+    e = cudaMemcpyAsync(din + off, hin + off, sbytes, cudaMemcpyHostToDevice, plan->h_up);
+    if (e == cudaSuccess) e = cudaEventRecord(plan->h_ev_up[j], plan->h_up);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->h_ev_up[j], 0);
+    if (e != cudaSuccess) break;
+    tcfft_status st = tcfft_exec_batch(plan, din + off, dout + off, per_slice, stream);
+    if (st != TCFFT_OK) {
+      cudaStreamSynchronize(plan->h_up);
+      cudaStreamSynchronize(s);
+      return st;
+    }
+    e = cudaEventRecord(plan->h_ev_done[j], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->h_down, plan->h_ev_done[j], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hout + off, dout + off, sbytes, cudaMemcpyDeviceToHost, plan->h_down);
+  }
+  const cudaError_t e1 = cudaStreamSynchronize(plan->h_up);
+  const cudaError_t e2 = cudaStreamSynchronize(s);
+  const cudaError_t e3 = cudaStreamSynchronize(plan->h_down);
   if (e != cudaSuccess) return from_cuda(e);
-  tcfft_status st = tcfft_exec(plan, plan->h_in_dev, plan->h_out_dev, stream);
-  if (st != TCFFT_OK) return st;
-  e = cudaMemcpyAsync(host_out, plan->h_out_dev, bytes, cudaMemcpyDeviceToHost, s);
-  if (e != cudaSuccess) return from_cuda(e);
-  e = cudaStreamSynchronize(s);
-  return from_cuda(e);
+  if (e1 != cudaSuccess) return from_cuda(e1);
+  if (e2 != cudaSuccess) return from_cuda(e2);
+  return from_cuda(e3);
 }
 
 tcfft_status tcfft_destroy(tcfft_plan plan) {
