@@ -132,45 +132,9 @@ void encode_out_map(PassParams& p, bool split) {
 
 void encode_in_map(PassParams& p, bool split) {
   if (!p.in_tma) return;
-  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  const bool f32 = split && p.in_f32;
-  const uint64_t elem = f32 ? 8 : 4;
-  const int64_t I1 = int64_t(1) << p.log2I1;
-  const bool lvl2 = p.log2I2 < 40;  // a bounded second index level
-  const int64_t I2 = lvl2 ? (int64_t(1) << p.log2I2) : 0;
-  const int64_t L = int64_t(1) << p.log2N;
-  const int64_t T = p.T;
-  // dims (innermost first): t1, element, t2, t3, plane; size-1 dims get a
-  // 16-byte stride that is never stepped
-  cuuint64_t dims[5], strides[4];
-  dims[0] = (cuuint64_t)I1;
-  dims[1] = (cuuint64_t)L;
-  strides[0] = (cuuint64_t)p.in_l.es * elem;
-  if (lvl2) {
-    dims[2] = (cuuint64_t)I2;
-    dims[3] = (cuuint64_t)(T / (I1 * I2));
-  } else {
-    dims[2] = (cuuint64_t)(T / I1);
-    dims[3] = 1;
-  }
-  strides[1] = (cuuint64_t)p.in_l.s2 * elem;
-  strides[2] = (cuuint64_t)p.in_l.s3 * elem;
-  dims[4] = (split && !f32) ? 2 : 1;
-  strides[3] = (cuuint64_t)p.in_plane * 4;
-  for (int i = 2; i <= 4; ++i)
-    if (dims[i] == 1) strides[i - 1] = 16;
-  bool ok = enc != nullptr && T % I1 == 0 && (!lvl2 || T % (I1 * I2) == 0);
-  for (int i = 0; i < 4 && ok; ++i) ok = strides[i] % 16 == 0 && strides[i] > 0 && strides[i] < (1ull << 40);
-  for (int i = 0; i < 5 && ok; ++i) ok = dims[i] >= 1 && dims[i] <= (1ull << 32);
-  const cuuint32_t box[5] = {(cuuint32_t)(1u << p.log2C), (cuuint32_t)std::min<int64_t>(L, 256), 1, 1, 1};
-  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-  ok = ok && box[0] <= 256 && (box[0] * elem) % 16 == 0;
-  if (ok)
-    ok = enc(&p.in_map, f32 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 5,
-             const_cast<uint32_t*>(p.in), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-  if (!ok) p.in_tma = 0;
+  if (!encode_side_map(&p.in_map, p, p.in_l, p.in, p.in_plane, split && p.in_f32, split,
+                       CU_TENSOR_MAP_SWIZZLE_NONE))
+    p.in_tma = 0;
 }
 
 int ilog2(int64_t v) {
