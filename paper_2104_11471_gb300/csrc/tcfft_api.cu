@@ -651,6 +651,9 @@ tcfft_status finish(tcfft_plan_s* pl, tcfft_status st, tcfft_plan* out) {
   if (st != TCFFT_OK) {
     delete pl;
     *out = nullptr;
+    // a failed allocation leaves the runtime's last-error state set; clear it
+    // so that later launch checks (of this or other plans) do not report it
+    (void)cudaGetLastError();
     return st;
   }
   *out = pl;
@@ -906,12 +909,14 @@ tcfft_status tcfft_exec_host(tcfft_plan plan, const void* host_in, void* host_ou
   if (!plan->h_in_dev) {
     if (cudaMalloc(&plan->h_in_dev, bytes) != cudaSuccess) {
       plan->h_in_dev = nullptr;
+      (void)cudaGetLastError();  // not a sticky error: clear it for later checks
       return TCFFT_ERR_ALLOC;
     }
     if (cudaMalloc(&plan->h_out_dev, bytes) != cudaSuccess) {
       cudaFree(plan->h_in_dev);
       plan->h_in_dev = nullptr;
       plan->h_out_dev = nullptr;
+      (void)cudaGetLastError();
       return TCFFT_ERR_ALLOC;
     }
   }
