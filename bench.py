@@ -572,6 +572,10 @@ def run_gpu(args, world, rank, local):
 
     import paper_2104_11471_gb300 as tc
 
+    # one rank compiles (if the library is out of date), the others then load it
+    if local == 0:
+        tc.build()
+    barrier(world)
     tc.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
