@@ -286,7 +286,6 @@ def build_sweep(args, dev, rank):
     in plain FP16 (the benchmark), split FP16 or FP32 in and out."""
     import numpy as np
     import torch
-    import oracle
     import paper_2104_11471_gb300 as tc
     sizes = [int(s) for s in args.sizes.split(",")] if args.sizes else SWEEP
     prec = args.precision
@@ -310,7 +309,7 @@ def build_sweep(args, dev, rank):
         b = POINTS // n
         plan = tc.Plan.plan_1d(n, b, code, 0 if args.no_autotune else tc.TCFFT_PLAN_AUTOTUNE)
 
-        def check(y=y, n=n, b=b):
+        def check(orc, y=y, n=n, b=b):
             row = b // 2  # one transform from the middle of the batch
             sl = slice(row * 2 * n, (row + 1) * 2 * n)
             xin = h[sl].astype(np.float64)
@@ -321,8 +320,8 @@ def build_sweep(args, dev, rank):
             if prec == "split":
                 xin = xin + lo[sl].astype(np.float64) / 2048.0
                 out = out + y[2 * POINTS:][sl].cpu().numpy().view(np.float16).astype(np.float64) / 2048.0
-            ref = oracle.fft_batch((xin[0::2] + 1j * xin[1::2])[None, :])[0]
-            return oracle.rel_l2(out[0::2] + 1j * out[1::2], ref)
+            ref = orc.fft_batch((xin[0::2] + 1j * xin[1::2])[None, :])[0]
+            return orc.rel_l2(out[0::2] + 1j * out[1::2], ref)
         entries.append(Entry(f"1d n={n} batch={b}", plan, x, y, flops_1d(n, b), bpp * n * b, check))
     cfg = {"workload": f"1d_sweep: N=2^8..2^24 step 2^2, batch=2^{args.log2_points}/N, "
                        "one exec per size per step, uniform[-1,1] seeded inputs",
@@ -337,7 +336,6 @@ def build_2d(args, dev, rank):
     """Batched 2D: sides 256, 512, 1024, 4096, 8192, batch = 2^28 / side^2, plain and split."""
     import numpy as np
     import torch
-    import oracle
     import paper_2104_11471_gb300 as tc
     sides = [int(s) for s in args.sizes.split(",")] if args.sizes else [256, 512, 1024, 4096, 8192]
     hi, lo = _split_draw(2 * POINTS, 2000 + rank)
@@ -353,7 +351,7 @@ def build_2d(args, dev, rank):
             xs = x if split else x[:2 * POINTS]
             ys = y if split else y[:2 * POINTS]
 
-            def check(y=y, side=side, b=b, split=split):
+            def check(orc, y=y, side=side, b=b, split=split):
                 m = side * side
                 row = b // 2
                 sl = slice(row * 2 * m, (row + 1) * 2 * m)
@@ -364,9 +362,9 @@ def build_2d(args, dev, rank):
                     o_lo = y[2 * POINTS:][sl].cpu().numpy().view(np.float16).astype(np.float64)
                     o_hi = o_hi + o_lo / 2048.0
                 z = (xin[0::2] + 1j * xin[1::2]).reshape(side, side)
-                ref = oracle.fft_2d(z)
+                ref = orc.fft_2d(z)
                 got = (o_hi[0::2] + 1j * o_hi[1::2]).reshape(side, side)
-                return oracle.rel_l2(got, ref)
+                return orc.rel_l2(got, ref)
             entries.append(Entry(f"2d {side}x{side} batch={b} {'split' if split else 'plain'}", plan, xs, ys,
                                  5.0 * side * side * math.log2(side * side) * b,
                                  (16.0 if split else 8.0) * side * side * b, check))
@@ -396,7 +394,6 @@ def build_ragged(args, dev, rank):
     pass is timed beside it."""
     import numpy as np
     import torch
-    import oracle
     import paper_2104_11471_gb300 as tc
     shapes = ragged_shapes(4 + rank)
     pts = sum(int(np.prod(sh)) for sh in shapes)
@@ -408,7 +405,7 @@ def build_ragged(args, dev, rank):
     flops = sum(5.0 * np.prod(sh) * math.log2(np.prod(sh)) for sh in shapes)
     offs = np.concatenate([[0], np.cumsum([int(np.prod(sh)) for sh in shapes])])
 
-    def check(y=y):
+    def check(orc, y=y):
         worst = 0.0
         picks = [i for i, sh in enumerate(shapes) if len(sh) == 2][:2] + \
                 [i for i, sh in enumerate(shapes) if len(sh) == 1][:6]
@@ -418,8 +415,8 @@ def build_ragged(args, dev, rank):
             out = y[2 * a:2 * b].cpu().numpy().view(np.float16).astype(np.float64)
             z = (xin[0::2] + 1j * xin[1::2]).reshape(shapes[i])
             g = (out[0::2] + 1j * out[1::2]).reshape(shapes[i])
-            ref = oracle.fft_batch(z) if len(shapes[i]) == 1 else oracle.fft_2d(z)
-            worst = max(worst, oracle.rel_l2(g, ref))
+            ref = orc.fft_batch(z) if len(shapes[i]) == 1 else orc.fft_2d(z)
+            worst = max(worst, orc.rel_l2(g, ref))
         return worst
     entries = [Entry(f"ragged {len(shapes)} transforms, one graph launch", plan, x, y, flops, 8.0 * pts, check)]
     cfg = {"workload": "ragged: 4096 1D transforms N=2^k, k~U{8..16}, + 256 2D transforms side~U{128,256,512,1024}, "
@@ -643,13 +640,6 @@ def run_gpu(args, world, rank, local):
 
     compare = aux(args.steps, stream) if aux else None
 
-    # accuracy of the timed outputs: one sampled transform per exec vs the FP64 oracle
-    if not args.no_check:
-        for i, e in enumerate(entries):
-            e.plan.exec(e.x, e.y, stream)
-            torch.cuda.synchronize()
-            per[i]["rel_l2"] = float(f"{e.check():.3e}")
-
     # end to end: pinned host buffers through tcfft_exec_host
     e2e = None
     if not args.no_e2e:
@@ -668,6 +658,15 @@ def run_gpu(args, world, rank, local):
         e2e = {"value": world * flops_step * e2e_steps / e2e_s / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": io, "d2h_bytes_per_step": io}
 
+    # CPU oracle leg (the FP64 oracle on the host cores): the accuracy of the
+    # timed outputs (one sampled transform per exec, recomputed on the host)
+    # and the CPU baseline
+    if not args.no_check:
+        import oracle
+        for i, e in enumerate(entries):
+            e.plan.exec(e.x, e.y, stream)
+            torch.cuda.synchronize()
+            per[i]["rel_l2"] = float(f"{e.check(oracle):.3e}")
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         if args.workload == "sweep1d":
