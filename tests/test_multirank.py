@@ -89,3 +89,29 @@ def test_write_traffic_keeps_the_timed_step(tmp_path, monkeypatch):
     d = json.load(open(tmp_path / "profiles" / "traffic_sweep1d.json"))
     assert d["measured_bytes_per_step_at_2^26_points"] == 1000 + 500 + 2000 + 700
     assert d["traffic_bytes_per_step"] == 4 * 4200 and d["launches_per_step"] == 2 and d["kernel_hash"] == "h"
+
+
+def test_clock_sampler_summary(tmp_path, monkeypatch):
+    # nvidia-smi samples (index, sm MHz, max MHz, power, active mask, hw slowdown,
+    # hw thermal, sw thermal, sw power cap) -> median SM clock and the reasons seen
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("TCFFT_CLOCKS_DIR", str(tmp_path))
+    cs = bench.ClockSampler(0)
+    lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "0, 2055, 2070, 1390.5, 0x4, Not Active, Not Active, Not Active, Active",
+             "0, 2070, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "garbage line"]
+    with open(cs.path, "w") as f:
+        f.write("\n".join(lines) + "\n")
+
+    class _Proc:  # a sampler that already exited
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+    cs.proc = _Proc()
+    cs.f = open(os.devnull, "w")
+    out = cs.stop()
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
