@@ -168,6 +168,11 @@ static void r2_rec(const cplx* x, int64_t stride, int64_t n, cplx* out, const cp
     cplx e = out[k];
 #if defined(ORACLE_PLANT) && ORACLE_PLANT == 3
     cplx o = cmul(tw[(k * step + step) % (ntop / 2 > 0 ? ntop / 2 : 1)], out[k + h]); /* planted: twiddle index off by one */
+#elif defined(ORACLE_PLANT) && ORACLE_PLANT == 6
+    /* planted: in the last merge, the twiddle of one thin output slice
+     * (k = 3 mod ntop/16) is taken ntop/8 entries too far */
+    int64_t ti = (n == ntop && ntop >= 64 && k % (ntop / 16) == 3) ? (k * step + ntop / 8) % (ntop / 2) : k * step;
+    cplx o = cmul(tw[ti], out[k + h]);
 #else
     cplx o = cmul(tw[k * step], out[k + h]);
 #endif

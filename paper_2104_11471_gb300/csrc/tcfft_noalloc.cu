@@ -46,7 +46,10 @@ static __device__ __align__(256) float2 g_noalloc_tw[(kMaxLog2 + 1) * 2 * kTwHal
 static __device__ __align__(256) float4 g_noalloc_stage[13 * kStageSlot];
 // DFT-matrix images for leading radix 1, 2, 4, 8 (16 images of 1024 halves each).
 static __device__ __align__(256) __half g_noalloc_dftb[4 * 16 * 1024];
-// Device-side error word of the kernels launched here.
+// Error word the pass kernels require (they write TCFFT_ERR_TIMEOUT into it
+// when a bounded wait expires).  Here it is write-only: zeroed once at set-up,
+// never read or cleared afterwards, because this entry point has no plan to
+// report device-side timeouts through.
 static __device__ __align__(256) int g_noalloc_status;
 
 namespace {

@@ -78,3 +78,24 @@ def sweep_seed(log2n: int) -> int:
 
 def seed_2d(log2side: int) -> int:
     return 2000 + log2side
+
+
+# ------------------------------------------------------- structured inputs
+def delta(shape, pos) -> np.ndarray:
+    """FP64 complex array of `shape` with a single 1 at index `pos` (a tuple
+    for 2D shapes), zero elsewhere."""
+    z = np.zeros(shape, dtype=np.complex128)
+    z[pos] = 1.0
+    return z
+
+
+def tone(n: int, k0: int, amp: float) -> np.ndarray:
+    """amp * exp(+2 pi i k0 t / n), t = 0 .. n-1, with the phase index reduced
+    mod n in integers so that large n keep full accuracy (FP64 complex)."""
+    t = (np.int64(k0) * np.arange(n, dtype=np.int64)) % n
+    return amp * np.exp(2j * np.pi * t / n)
+
+
+def tone_2d(nx: int, ny: int, k1: int, k2: int, amp: float) -> np.ndarray:
+    """amp * exp(+2 pi i (k1 t1 / nx + k2 t2 / ny)) on an nx x ny grid."""
+    return tone(nx, k1, 1.0)[:, None] * tone(ny, k2, amp)[None, :]

@@ -102,7 +102,7 @@ def test_fp32_round_trip(n):
     finally:
         fwd.destroy()
         inv.destroy()
-    check_rows(back, _c128(x), 4 * SPLIT_TOL, f"FP32 round trip N={n}")
+    check_rows(back, _c128(x), 4 * SPLIT_TOL, f"FP32 round trip N={n}", c=2.0)
 
 
 def test_fp32_exec_batch_prefix():

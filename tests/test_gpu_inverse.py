@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import seeded_inputs as si
-from gpu_helpers import PLAIN_TOL, SPLIT_TOL, check_rows, run_plan, to_device
+from gpu_helpers import PLAIN_TOL, SPLIT_TOL, U_PLAIN, U_SPLIT, check_elems, check_rows, run_plan, to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -53,6 +53,9 @@ def test_round_trip_plain(shape):
     inv.destroy()
     back = si.as_complex128(z.cpu().numpy().view(np.float16).reshape((batch,) + shape + (2,)))
     assert oracle.rel_l2(back, si.as_complex128(h)) < 3e-3
+    # two transforms' roundings: twice the per-element bound
+    check_elems(back.reshape(batch, -1), si.as_complex128(h).reshape(batch, -1), U_PLAIN, f"round trip {shape}",
+                c=2.0)
 
 
 def test_round_trip_split_is_near_fp32():
@@ -70,7 +73,9 @@ def test_round_trip_split_is_near_fp32():
     fwd.destroy()
     inv.destroy()
     o = z.cpu().numpy().view(np.float16).reshape((2, batch) + shape + (2,))
-    assert oracle.rel_l2(si.split_value(o[0], o[1]), si.split_value(hi, lo)) < 4 * SPLIT_TOL
+    back, x = si.split_value(o[0], o[1]), si.split_value(hi, lo)
+    assert oracle.rel_l2(back, x) < 4 * SPLIT_TOL
+    check_elems(back, x, U_SPLIT, "split round trip", c=2.0)
 
 
 def test_forward_scale_flag():

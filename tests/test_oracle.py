@@ -262,7 +262,7 @@ def _pins_catch(v):
     return failures
 
 
-@pytest.mark.parametrize("plant", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("plant", [1, 2, 3, 4, 5, 6])
 def test_planted_mistakes_are_caught(plant, tmp_path):
     v = oracle.planted_variant(plant, str(tmp_path))
     assert _pins_catch(v) > 0
