@@ -217,6 +217,8 @@ tcfft_status bind_tables(tcfft_plan_s* pl, Pass& ps, int log2L, int otw_level, i
 tcfft_status tune_pass(tcfft_plan_s* pl, Pass& ps, int64_t L, int64_t T, int64_t I1, int64_t I2, Side in,
                        Side out, int otw_level, int log2M);
 
+PassParams bound_params(const tcfft_plan_s* plan, const Pass& ps, const void* in, void* out);
+
 tcfft_status add_pass(tcfft_plan_s* pl, int64_t L, int64_t T, int64_t I1, int64_t I2, Side in,
                       Side out, Buf src, Buf dst, int otw_level, int log2M, int group = 0,
                       int64_t src_off = 0, int64_t dst_off = 0) {
@@ -424,48 +426,50 @@ tcfft_status tune_pass(tcfft_plan_s* pl, Pass& ps, int64_t L, int64_t T, int64_t
 
 constexpr int64_t kNoLevel = int64_t(1) << 40;  // "unbounded" index level
 
-tcfft_status plan_1d(tcfft_plan_s* pl) {
+// Longest strided pass (log2) for the plan's precision: split kernels keep
+// two planes per point, so their strided passes stop one length earlier.
+int max_strided_log2(const tcfft_plan_s* pl) { return max_log2_pass(kModeStrided, pl->split); }
+
+tcfft_status alloc_ws(tcfft_plan_s* pl, size_t bytes) {
+  if (pl->ws && pl->ws_bytes >= bytes) return TCFFT_OK;
+  cudaFree(pl->ws);
+  pl->ws = nullptr;
+  pl->ws_bytes = 0;
+  if (cudaMalloc(&pl->ws, bytes) != cudaSuccess) {
+    pl->ws = nullptr;
+    return TCFFT_ERR_ALLOC;
+  }
+  pl->ws_bytes = bytes;
+  return TCFFT_OK;
+}
+
+// The passes of a 1D transform n = 2^l[0] (one pass), 2^l[0] 2^l[1] (two
+// passes) or 2^l[0] 2^l[1] 2^l[2] (three passes); the workspace must exist
+// for more than one pass.
+tcfft_status build_1d(tcfft_plan_s* pl, const int* l, int np) {
   const int64_t n = pl->n, B = pl->batch;
-  const int64_t single = std::min<int64_t>(pl->split ? kSingleSplit : kSinglePlain,
-                                           int64_t(1) << env_int("TCFFT_SINGLE_MAX_LOG2", 14));  // tuning override
-  if (n <= single) {
+  if (np == 1) {
     Side s{n, 0, 0, 1};
     return add_pass(pl, n, B, kNoLevel, 1, s, s, BUF_IN, BUF_OUT, 0, 0);
   }
   const int lg = ilog2(n);
-  pl->ws_bytes = (size_t)B * n * 4 * (pl->split ? 2 : 1);
-  if (cudaMalloc(&pl->ws, pl->ws_bytes) != cudaSuccess) {
-    pl->ws = nullptr;
-    return TCFFT_ERR_ALLOC;
-  }
-  // three passes from 2^22 (tuning override TCFFT_THREE_PASS_MIN), always
-  // beyond 2^24, and for split precision beyond 2^22 (the four-step split
-  // would need strided passes longer than the split kernels' 2^11).  Measured
-  // at 2^28 points: 2^22 as 16 x 512 x 512 1.53 ms (2048 x 2048: 1.92 ms,
-  // 64 x 256 x 256: 1.62 ms); 2^23 as 128 x 256 x 256 1.61 ms (two passes:
-  // 2.65 ms); 2^24 as 256^3 1.45 ms (16 x 1024 x 1024: 1.75 ms).
-  const bool three = lg >= env_int("TCFFT_THREE_PASS_MIN", 22) || lg > 24 || (pl->split && lg > 22);
-  if (three) {
+  if (np == 3) {
     // n = N1 N2 N3 (M = N2 N3) in three passes of short transforms, so that
     // every pass keeps small per-CTA tiles with prefetch:
     //  A: N1-point DFTs of the columns x[M n1 + m], times W_n^{m k1} -> ws
     //  B: N2-point DFTs of ws[k1 M + N3 n2 + n3], times W_M^{n3 k2}, in place
     //  C: N3-point DFTs of ws rows (k1, k2) -> X[k1 + N1 k2 + N1 N2 k3]
-    const int l1_default = lg == 22 ? 4 : (lg == 23 ? 7 : 8);
-    const int l1 = std::max(4, std::min(8, env_int("TCFFT_THREE_PASS_L1", l1_default)));  // tuning override
-    const int l2 = (lg - l1 + 1) / 2, l3 = lg - l1 - l2;
-    const int64_t N1 = int64_t(1) << l1, N2 = int64_t(1) << l2, N3 = int64_t(1) << l3, M = N2 * N3;
+    const int64_t N1 = int64_t(1) << l[0], N2 = int64_t(1) << l[1], N3 = int64_t(1) << l[2], M = N2 * N3;
     Side a{1, n, 0, M};
     tcfft_status st = add_pass(pl, N1, B * M, M, kNoLevel, a, a, BUF_IN, BUF_WS, 1, lg);
     if (st != TCFFT_OK) return st;
     Side b{1, M, n, N3};
-    st = add_pass(pl, N2, B * N1 * N3, N3, N1, b, b, BUF_WS, BUF_WS, 1, l2 + l3);
+    st = add_pass(pl, N2, B * N1 * N3, N3, N1, b, b, BUF_WS, BUF_WS, 1, l[1] + l[2]);
     if (st != TCFFT_OK) return st;
     Side cin{M, N3, n, 1}, cout{1, N1, n, N1 * N2};
     return add_pass(pl, N3, B * N1 * N2, N1, N2, cin, cout, BUF_WS, BUF_OUT, 0, 0);
   }
-  const int l1 = env_int("TCFFT_FOUR_STEP_L1", (lg + 1) / 2);  // tuning override
-  const int64_t N1 = int64_t(1) << l1, N2 = n / N1;
+  const int64_t N1 = int64_t(1) << l[0], N2 = n / N1;
   // pass 1: columns n2 of length N1 (stride N2), times W_n^{n2 k1}
   Side c1{1, n, 0, N2};
   tcfft_status st = add_pass(pl, N1, B * N2, N2, kNoLevel, c1, c1, BUF_IN, BUF_WS, 1, lg);
@@ -475,32 +479,156 @@ tcfft_status plan_1d(tcfft_plan_s* pl) {
   return add_pass(pl, N2, B * N1, N1, kNoLevel, in2, out2, BUF_WS, BUF_OUT, 0, 0);
 }
 
-tcfft_status plan_2d(tcfft_plan_s* pl) {
+// Times the plan's current passes on the autotuning scratch (in = out =
+// scratch, the workspace between them): mean of three runs after a warm-up,
+// in ms; a negative value when a launch fails.
+float time_passes(tcfft_plan_s* pl) {
+  const size_t need = pl->io_bytes() + 4096;
+  if (pl->tune_bytes < need) {
+    cudaFree(pl->tune_buf);
+    pl->tune_buf = nullptr;
+    pl->tune_bytes = 0;
+    if (cudaMalloc(&pl->tune_buf, need) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return -1.0f;
+    }
+    cudaMemset(pl->tune_buf, 0, need);
+    pl->tune_bytes = need;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float total = 0.0f;
+  bool ok = true;
+  for (int rep = 0; rep < 4 && ok; ++rep) {
+    cudaEventRecord(e0);
+    for (const Pass& ps : pl->passes) {
+      PassParams p = bound_params(pl, ps, pl->tune_buf, pl->tune_buf);
+      void* args[1] = {&p};
+      if (launch_pass(ps.fn, ps.grid, ps.threads, ps.smem, 0, args) != cudaSuccess) ok = false;
+    }
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float t = 0.0f;
+    cudaEventElapsedTime(&t, e0, e1);
+    if (rep > 0) total += t;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!ok) {
+    (void)cudaGetLastError();
+    return -1.0f;
+  }
+  return total / 3.0f;
+}
+
+// The pass splits the planner may use for a multi-pass 1D transform of
+// 2^lg points: two passes N1 x N2 near the square root, three passes
+// N1 x N2 x N3 with N1 from 16 to 256 and N2 ~ N3, every factor a pass
+// length the strided kernels have (16 .. 4096 plain, .. 2048 split).
+std::vector<std::vector<int>> split_candidates(const tcfft_plan_s* pl, int lg) {
+  const int mx = max_strided_log2(pl);
+  std::vector<std::vector<int>> c;
+  for (int l1 = std::max(4, lg - mx); l1 <= std::min(mx, lg - 4); ++l1)
+    if (std::abs(2 * l1 - lg) <= 4) c.push_back({l1, lg - l1});
+  if (lg >= 20) {
+    for (int l1 = 4; l1 <= 8; ++l1) {
+      const int l2 = (lg - l1 + 1) / 2, l3 = lg - l1 - l2;
+      if (l3 >= 4 && l2 <= mx) c.push_back({l1, l2, l3});
+    }
+  }
+  return c;
+}
+
+// The split the planner takes without autotuning (measured at 2^28 points):
+// one pass to 16384; two passes N1 x N2, N1 = 2^ceil(lg/2), to 2^21; three
+// passes from 2^22 (tuning override TCFFT_THREE_PASS_MIN), always beyond
+// 2^24 and for split precision beyond 2^22 (the four-step split would need
+// strided passes longer than the split kernels' 2^11).  2^22 as 16 x 512 x
+// 512 1.53 ms (2048 x 2048: 1.92 ms, 64 x 256 x 256: 1.62 ms); 2^23 as 128 x
+// 256 x 256 1.61 ms (two passes: 2.65 ms); 2^24 as 256^3 1.45 ms (16 x 1024 x
+// 1024: 1.75 ms).
+std::vector<int> default_split(const tcfft_plan_s* pl, int lg) {
+  const bool three = lg >= env_int("TCFFT_THREE_PASS_MIN", 22) || lg > 24 || (pl->split && lg > 22);
+  if (three) {
+    const int l1_default = lg == 22 ? 4 : (lg == 23 ? 7 : 8);
+    const int l1 = std::max(4, std::min(8, env_int("TCFFT_THREE_PASS_L1", l1_default)));  // tuning override
+    const int l2 = (lg - l1 + 1) / 2;
+    return {l1, l2, lg - l1 - l2};
+  }
+  const int l1 = env_int("TCFFT_FOUR_STEP_L1", (lg + 1) / 2);  // tuning override
+  return {l1, lg - l1};
+}
+
+tcfft_status plan_1d(tcfft_plan_s* pl) {
+  const int64_t n = pl->n, B = pl->batch;
+  const int64_t single = std::min<int64_t>(pl->split ? kSingleSplit : kSinglePlain,
+                                           int64_t(1) << env_int("TCFFT_SINGLE_MAX_LOG2", 14));  // tuning override
+  const int lg = ilog2(n);
+  if (n <= single) {
+    const int l[1] = {lg};
+    return build_1d(pl, l, 1);
+  }
+  tcfft_status st = alloc_ws(pl, (size_t)B * n * 4 * (pl->split ? 2 : 1));
+  if (st != TCFFT_OK) return st;
+  std::vector<int> best = default_split(pl, lg);
+  if (pl->autotune) {
+    // time every candidate split (each pass with its own tuned geometry) on
+    // the plan's sizes; the winner is cached per (length, precision, batch)
+    char key[128];
+    std::snprintf(key, sizeof(key), "split_v1_lg%d_s%d_T%d_h%d", lg, pl->split ? 1 : 0, ilog2(B),
+                  pl->share_sm ? 1 : 0);
+    int64_t code = -1;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      tune_load();
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) code = it->second;
+    }
+    if (code < 0) {
+      float best_ms = 1e30f;
+      for (const std::vector<int>& c : split_candidates(pl, lg)) {
+        pl->passes.clear();
+        if (build_1d(pl, c.data(), (int)c.size()) != TCFFT_OK) continue;
+        const float ms = time_passes(pl);
+        if (ms > 0.0f && ms < best_ms) {
+          best_ms = ms;
+          code = 0;
+          for (size_t i = 0; i < c.size(); ++i) code |= (int64_t)c[i] << (8 * i);
+        }
+      }
+      pl->passes.clear();
+      if (code >= 0) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = code;
+        tune_store();
+      }
+    }
+    if (code > 0) {
+      best.clear();
+      for (int i = 0; i < 3 && ((code >> (8 * i)) & 255); ++i) best.push_back((int)((code >> (8 * i)) & 255));
+    }
+  }
+  return build_1d(pl, best.data(), (int)best.size());
+}
+
+// The passes of a 2D transform: rows, then columns in one strided pass
+// (col_l1 == 0) or in two passes nx = N1 N2 with N1 = 2^col_l1 (the
+// workspace must exist then).
+tcfft_status build_2d(tcfft_plan_s* pl, int col_l1) {
   const int64_t nx = pl->nx, ny = pl->ny, B = pl->batch;
   const int64_t mat = nx * ny;
   // rows: nx * B transforms of length ny, contiguous
   Side r{ny, 0, 0, 1};
   tcfft_status st = add_pass(pl, ny, B * nx, kNoLevel, 1, r, r, BUF_IN, BUF_OUT, 0, 0);
   if (st != TCFFT_OK) return st;
-  const int64_t cap = pl->split ? kCapSplit : kCapPlain;
-  // one column pass up to 2048 rows; longer columns in two passes, 16 x nx/16
-  // (measured at 2^28 points: 4096^2 plain 2.27 -> 1.48 ms, split 3.81 ->
-  // 2.97 ms; 8192^2 plain 1.91 -> 1.64 ms against 128 x 64, split 4.88 -> 3.70;
-  // 1024^2 keeps its single pass, 1.16 ms against 1.61 ms for 16 x 64)
-  const int col_max = env_int("TCFFT_2D_COL_MAX_LOG2", 11);  // tuning override
-  if (8 * nx <= cap && ilog2(nx) <= col_max) {
+  if (col_l1 == 0) {
     // columns: ny * B transforms of length nx, stride ny, in place on out
     Side c{1, mat, 0, ny};
     return add_pass(pl, nx, B * ny, ny, kNoLevel, c, c, BUF_OUT, BUF_OUT, 0, 0);
   }
-  // columns too long for one CTA group: nx = N1 N2 in two passes
   const int lg = ilog2(nx);
-  const int64_t N1 = int64_t(1) << env_int("TCFFT_2D_COL_L1", 4), N2 = nx / N1;  // tuning override
-  pl->ws_bytes = (size_t)B * mat * 4 * (pl->split ? 2 : 1);
-  if (cudaMalloc(&pl->ws, pl->ws_bytes) != cudaSuccess) {
-    pl->ws = nullptr;
-    return TCFFT_ERR_ALLOC;
-  }
+  const int64_t N1 = int64_t(1) << col_l1, N2 = nx / N1;
   // pass A: element n1 of column (iy, n2) at (N2 n1 + n2) ny + iy
   Side a{1, ny, mat, N2 * ny};
   st = add_pass(pl, N1, B * ny * N2, ny, N2, a, a, BUF_OUT, BUF_WS, 2, lg);
@@ -508,6 +636,69 @@ tcfft_status plan_2d(tcfft_plan_s* pl) {
   // pass B: row k1 (elements n2 at (N2 k1 + n2) ny + iy) -> X[k1 + N1 k2]
   Side bi{1, N2 * ny, mat, ny}, bo{1, ny, mat, N1 * ny};
   return add_pass(pl, N2, B * ny * N1, ny, N1, bi, bo, BUF_WS, BUF_OUT, 0, 0);
+}
+
+tcfft_status plan_2d(tcfft_plan_s* pl) {
+  const int64_t nx = pl->nx, B = pl->batch;
+  const int64_t mat = nx * pl->ny;
+  const int64_t cap = pl->split ? kCapSplit : kCapPlain;
+  const int lg = ilog2(nx);
+  const size_t ws = (size_t)B * mat * 4 * (pl->split ? 2 : 1);
+  // one column pass up to 2048 rows; longer columns in two passes, 16 x nx/16
+  // (measured at 2^28 points: 4096^2 plain 2.27 -> 1.48 ms, split 3.81 ->
+  // 2.97 ms; 8192^2 plain 1.91 -> 1.64 ms against 128 x 64, split 4.88 -> 3.70;
+  // 1024^2 keeps its single pass, 1.16 ms against 1.61 ms for 16 x 64)
+  const int col_max = env_int("TCFFT_2D_COL_MAX_LOG2", 11);  // tuning override
+  const bool one_ok = 8 * nx <= cap && lg <= std::min(col_max, max_strided_log2(pl));
+  int col_l1 = one_ok ? 0 : env_int("TCFFT_2D_COL_L1", 4);  // tuning override
+  if (pl->autotune) {
+    // candidates: one column pass (where it fits) and two passes N1 x N2
+    // with N1 = 16 .. 128, each timed with its passes' tuned geometry
+    std::vector<int> cands;
+    if (8 * nx <= cap && lg <= max_strided_log2(pl)) cands.push_back(0);
+    for (int l1 = 4; l1 <= 7; ++l1)
+      if (lg - l1 >= 4 && lg - l1 <= max_strided_log2(pl) && lg >= 8) cands.push_back(l1);
+    if (cands.size() > 1) {
+      char key[128];
+      std::snprintf(key, sizeof(key), "col_v1_nx%d_ny%d_s%d_T%d_h%d", lg, ilog2(pl->ny), pl->split ? 1 : 0,
+                    ilog2(B), pl->share_sm ? 1 : 0);
+      int64_t code = -1;
+      {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        tune_load();
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) code = it->second;
+      }
+      if (code < 0 && alloc_ws(pl, ws) == TCFFT_OK) {
+        float best_ms = 1e30f;
+        for (int c : cands) {
+          pl->passes.clear();
+          if (build_2d(pl, c) != TCFFT_OK) continue;
+          const float ms = time_passes(pl);
+          if (ms > 0.0f && ms < best_ms) {
+            best_ms = ms;
+            code = c;
+          }
+        }
+        pl->passes.clear();
+        if (code >= 0) {
+          std::lock_guard<std::mutex> lock(g_tune_mu);
+          g_tune_cache[key] = code;
+          tune_store();
+        }
+      }
+      if (code >= 0) col_l1 = (int)code;
+    }
+  }
+  if (col_l1 > 0) {
+    tcfft_status st = alloc_ws(pl, ws);
+    if (st != TCFFT_OK) return st;
+  } else if (pl->ws) {
+    cudaFree(pl->ws);  // candidates needed it; the chosen plan does not
+    pl->ws = nullptr;
+    pl->ws_bytes = 0;
+  }
+  return build_2d(pl, col_l1);
 }
 
 // Ragged batch: transform i is 1D of length n0[i] (n1 == null or n1[i] == 0)
