@@ -97,6 +97,17 @@ __device__ __forceinline__ uint32_t a_off(uint32_t m, uint32_t k) {
          ((((mm & 63u) >> 3) ^ (k & 7u)) << 4) + ((mm & 7u) << 1);
 }
 
+// MMA row order.  Logical row r (a butterfly's identity at the current
+// stage) sits at physical row (TMEM lane, A row) rp(r) = r ^ (bit 6 of r) << 3,
+// an involution that swaps the two 8-row groups of each 16-row block in the
+// upper half of every 128-row tile.  Writers whose lanes fill consecutive
+// 16-row blocks at one K (the epilogues, the strided stage-1 load) then put
+// the first 8-row chunk of lanes 0-3 and of lanes 4-7 of a quarter-warp in
+// 16-byte slots of opposite parity: all eight 16-byte stores of a
+// quarter-warp land in distinct bank groups instead of two-way conflicts.
+// Tiles (rows >> 7) are unchanged, so per-tile DFT matrices still apply.
+__device__ __forceinline__ uint32_t rp(uint32_t r) { return r ^ (((r >> 6) & 1u) << 3); }
+
 __device__ __forceinline__ int64_t side_base(const SideLayout& l, int64_t t, int log2I1,
                                              int log2I2) {
   const int64_t t1 = t & ((int64_t(1) << log2I1) - 1);
@@ -167,10 +178,11 @@ __device__ __forceinline__ void small_dft(float2 (&v)[RX]) {
   }
 }
 
-// Writes 8 consecutive butterfly rows (m0 multiple of 8) of input k of A from
-// 8 packed complex values: re halves at K = k, im halves at K = 16 + k.
+// Writes 8 consecutive logical butterfly rows (m0 multiple of 8) of input k
+// of A from 8 packed complex values: re halves at K = k, im halves at K = 16 + k.
 __device__ __forceinline__ void a_store8c(uint8_t* A, uint32_t m0, uint32_t k,
                                           const uint32_t (&v)[8]) {
+  m0 = rp(m0);
   const uint4 re = make_uint4(__byte_perm(v[0], v[1], 0x5410), __byte_perm(v[2], v[3], 0x5410),
                               __byte_perm(v[4], v[5], 0x5410), __byte_perm(v[6], v[7], 0x5410));
   const uint4 im = make_uint4(__byte_perm(v[0], v[1], 0x7632), __byte_perm(v[2], v[3], 0x7632),
@@ -378,13 +390,23 @@ __device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, con
         }
       }
     } else {
+    // strided raw buffer written by swizzled tensor-map boxes: 16-byte slot
+    // index XOR (byte offset >> 7) & swm (swm = 0: plain layout)
+    const uint32_t swm = (SMEM && !K::IN_C) ? ((1u << p.in_swz) - 1u) : 0u;
 #pragma unroll
     for (int n0 = 0; n0 < RX; ++n0) {
       uint4 a = make_uint4(0, 0, 0, 0), b = a;
       const uint4* s4 = reinterpret_cast<const uint4*>(src + off0 + n0 * step);
       if constexpr (SMEM) {
-        a = s4[0];
-        b = s4[1];
+        if constexpr (!K::IN_C) {
+          uint32_t bo = (off0 + n0 * step) << 2;
+          bo ^= ((bo >> 7) & swm) << 4;
+          a = *reinterpret_cast<const uint4*>(reinterpret_cast<const uint8_t*>(src) + bo);
+          b = *reinterpret_cast<const uint4*>(reinterpret_cast<const uint8_t*>(src) + (bo ^ 16u));
+        } else {
+          a = s4[0];
+          b = s4[1];
+        }
       } else if (valid) {
         a = __ldg(s4);
         b = __ldg(s4 + 1);
@@ -395,8 +417,15 @@ __device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, con
         uint4 c2 = make_uint4(0, 0, 0, 0), d = c2;
         const uint4* l4 = reinterpret_cast<const uint4*>(src_lo + off0 + n0 * step);
         if constexpr (SMEM) {
-          c2 = l4[0];
-          d = l4[1];
+          if constexpr (!K::IN_C) {
+            uint32_t bo = (off0 + n0 * step) << 2;
+            bo ^= ((bo >> 7) & swm) << 4;
+            c2 = *reinterpret_cast<const uint4*>(reinterpret_cast<const uint8_t*>(src_lo) + bo);
+            d = *reinterpret_cast<const uint4*>(reinterpret_cast<const uint8_t*>(src_lo) + (bo ^ 16u));
+          } else {
+            c2 = l4[0];
+            d = l4[1];
+          }
         } else if (valid) {
           c2 = __ldg(l4);
           d = __ldg(l4 + 1);
@@ -459,11 +488,12 @@ __device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, con
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const uint32_t k = (uint32_t)(np + i);
-            *reinterpret_cast<uint16_t*>(A + a_off(g, k)) = (uint16_t)(hv[k0][i] & 0xFFFFu);
-            *reinterpret_cast<uint16_t*>(A + a_off(g, 16 + k)) = (uint16_t)(hv[k0][i] >> 16);
+            const uint32_t gp = rp(g);
+            *reinterpret_cast<uint16_t*>(A + a_off(gp, k)) = (uint16_t)(hv[k0][i] & 0xFFFFu);
+            *reinterpret_cast<uint16_t*>(A + a_off(gp, 16 + k)) = (uint16_t)(hv[k0][i] >> 16);
             if constexpr (K::SPLIT) {
-              *reinterpret_cast<uint16_t*>(Alo + a_off(g, k)) = (uint16_t)(lv[k0][i] & 0xFFFFu);
-              *reinterpret_cast<uint16_t*>(Alo + a_off(g, 16 + k)) = (uint16_t)(lv[k0][i] >> 16);
+              *reinterpret_cast<uint16_t*>(Alo + a_off(gp, k)) = (uint16_t)(lv[k0][i] & 0xFFFFu);
+              *reinterpret_cast<uint16_t*>(Alo + a_off(gp, 16 + k)) = (uint16_t)(lv[k0][i] >> 16);
             }
           }
         }
@@ -492,15 +522,17 @@ __device__ __forceinline__ void cmul2(float2& x, float2& y, float2 c, float2 d, 
 }
 
 // Byte offsets of the four 16-byte chunks a thread writes for one butterfly
-// (16 consecutive rows m0..m0+15 at input k of the next stage): re/im halves
-// of rows m0..m0+7 and m0+8..m0+15.  m0 is a multiple of 16.
+// (16 consecutive logical rows m0..m0+15 at input k of the next stage): re/im
+// halves of rows m0..m0+7 and m0+8..m0+15.  m0 is a multiple of 16; the two
+// 8-row groups sit in adjacent 16-byte slots (slot index ^ 1) whichever of
+// them rp() puts first.
 struct RowChunks {
   uint32_t re0, re1;  // im chunks are 2048 bytes further (K + 16)
 };
 __device__ __forceinline__ RowChunks row_chunks(uint32_t m0, uint32_t k) {
   RowChunks r;
-  r.re0 = a_off(m0, k);
-  r.re1 = r.re0 + ((k & 1u) ? -16 : 16);  // chunk index (2u+1) ^ k = ((2u) ^ k) ^ 1
+  r.re0 = a_off(rp(m0), k);
+  r.re1 = r.re0 ^ 16u;
   return r;
 }
 
@@ -676,7 +708,7 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
 
       const bool last = (j == K::S);
       for (int t = half; t < tiles; t += halves) {
-        const uint32_t row = (uint32_t)t * 128u + 32u * quarter + lane;
+        const uint32_t row = rp((uint32_t)t * 128u + 32u * quarter + lane);  // logical row of this lane
         // X[i] = (Re out 2i, Re out 2i+1), Y[i] = (Im out 2i, Im out 2i+1)
         float2 X[8], Y[8];
         {

@@ -72,6 +72,12 @@ struct PassParams {
   // elements), encoded at exec time for the bound pointer; 0 = per-thread
   // 16-byte cp.async gathers
   int in_tma;
+  // swizzle of the strided input boxes in shared memory (0 none; 1, 2, 3 =
+  // 32-, 64-, 128-byte spans matching rows of C = 8, 16, 32 columns): the
+  // 16-byte slot index of byte offset b within the raw buffer is XORed with
+  // (b >> 7) & (2^in_swz - 1), so the stage-1 reads of a quarter-warp spread
+  // over all bank groups
+  int in_swz;
   CUtensorMap in_map;  // 128-byte aligned by its type
   // strided output of a two-stage pass (length 256..1024, C in {8, 16, 32})
   // through tensor-map stores: the staging copy is written in the map's swizzle

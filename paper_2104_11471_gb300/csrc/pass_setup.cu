@@ -131,10 +131,27 @@ void encode_out_map(PassParams& p, bool split) {
 }
 
 void encode_in_map(PassParams& p, bool split) {
+  p.in_swz = 0;
   if (!p.in_tma) return;
-  if (!encode_side_map(&p.in_map, p, p.in_l, p.in, p.in_plane, split && p.in_f32, split,
-                       CU_TENSOR_MAP_SWIZZLE_NONE))
-    p.in_tma = 0;
+  // FP16 planes: rows of C x 4 bytes land in the matching 32/64/128-byte
+  // swizzle when every box and plane of the raw buffer starts on a 1 KB line
+  const bool f32 = split && p.in_f32;
+  const int rowb = 4 << p.log2C;
+  const int64_t P = int64_t(1) << (p.log2C + p.log2N);
+  int swz = 0;
+  if (!f32 && p.log2N >= 6 && (P * 4) % 1024 == 0) swz = rowb == 32 ? 1 : (rowb == 64 ? 2 : (rowb == 128 ? 3 : 0));
+  if (env_int("TCFFT_NO_IN_SWIZZLE", 0)) swz = 0;  // debugging override
+  const CUtensorMapSwizzle mode = swz == 1   ? CU_TENSOR_MAP_SWIZZLE_32B
+                                  : swz == 2 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                  : swz == 3 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                             : CU_TENSOR_MAP_SWIZZLE_NONE;
+  if (encode_side_map(&p.in_map, p, p.in_l, p.in, p.in_plane, f32, split, mode)) {
+    p.in_swz = swz;
+    return;
+  }
+  if (swz && encode_side_map(&p.in_map, p, p.in_l, p.in, p.in_plane, f32, split, CU_TENSOR_MAP_SWIZZLE_NONE))
+    return;
+  p.in_tma = 0;
 }
 
 int ilog2(int64_t v) {
