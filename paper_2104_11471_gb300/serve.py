@@ -19,6 +19,16 @@ device.  A scheduling loop on the host:
   does not wait for a large job's persistent grid to drain;
 * retires finished batches (CUDA events), releasing their memory.
 
+Admission counts everything the server holds on the device against the HBM
+budget: the input pool, every resident plan's own memory (workspace, twiddle
+tables, DFT-matrix images: tcfft_workspace_bytes) and the input and output
+buffers of the batches in flight.  A request whose plan is not resident
+brings the plan's estimated bytes with it; when the total would pass the
+budget, idle plans (no batch in flight) are destroyed, least recently used
+first, and a new plan that still does not fit is made for fewer transforms
+(its capacity halved down to the batch at hand).  Otherwise the request
+waits until running batches free memory.
+
 Latency is arrival to completion as seen by the host.  All transform work
 runs in libtcfft's kernels; this module only schedules, allocates and copies.
 """
@@ -104,8 +114,14 @@ class FFTServer:
         self.depth = depth                # batches in flight per stream
         self.job_points = job_points      # merge requests up to this many points
         self.plans = {}
+        self.plan_bytes = {}   # key -> device bytes the plan holds (tcfft_workspace_bytes)
+        self.plan_cap = {}     # key -> transforms per batch the plan was made for
+        self.plan_used = {}    # key -> last launch (monotonic counter), for LRU eviction
+        self.plan_jobs = {}    # key -> batches in flight
+        self.evictions = 0
         self.in_use = 0
         self.peak_in_use = 0
+        self.peak_plan_bytes = 0
         # seeded input pool on the device (hi plane, lo plane): requests read slices
         rng = np.random.default_rng(seed)
         v = rng.uniform(-1.0, 1.0, size=2 * pool_points)
@@ -115,28 +131,122 @@ class FFTServer:
         self.pool_hi = torch.from_numpy(hi.view(np.uint16)).cuda()
         self.pool_lo = torch.from_numpy(lo.view(np.uint16)).cuda()
         self.pool_host = (hi, lo)
+        self.pool_bytes = 2 * self.pool_hi.numel() * self.pool_hi.element_size()
 
     # ---------------------------------------------------------------- plans
-    def capacity(self, shape) -> int:
+    def capacity(self, shape, split: bool = False) -> int:
+        """Transforms per batch: the resident plan's, else the default
+        (max(64, job_points / transform size))."""
+        key = (tuple(shape), split)
+        if key in self.plan_cap:
+            return self.plan_cap[key]
         m = int(np.prod(shape))
         return max(64, self.job_points // m)
 
-    def plan(self, shape, split: bool) -> Plan:
+    def resident_bytes(self) -> int:
+        """Device memory held between batches: input pool + resident plans."""
+        return getattr(self, "pool_bytes", 0) + sum(self.plan_bytes.values())
+
+    def plan_estimate(self, shape, split: bool, cap: int) -> int:
+        """Device bytes a plan for `cap` transforms will hold: the multi-pass
+        workspace (1D beyond 16384 points, 2D columns beyond 2048 rows) plus
+        a margin for its tables and images (well under 1 MiB up to 2^20
+        points)."""
+        m = int(np.prod(shape))
+        planes = 2 if split else 1
+        multi = m > 16384 if len(shape) == 1 else shape[0] > 2048
+        return (cap * m * 4 * planes if multi else 0) + (1 << 20)
+
+    def _create_plan(self, shape, split: bool, cap: int):
+        prec = TCFFT_FP16_SPLIT if split else TCFFT_FP16
+        flags = TCFFT_PLAN_SHARE_SM if self.share_sm else 0
+        p = (Plan.plan_1d(shape[0], cap, prec, flags) if len(shape) == 1
+             else Plan.plan_2d(shape[0], shape[1], cap, prec, flags))
+        return p, p.workspace_bytes
+
+    def _destroy_plan(self, key):
+        p = self.plans.pop(key, None)
+        if p is not None:
+            p.destroy()
+        self.plan_bytes.pop(key, None)
+        self.plan_cap.pop(key, None)
+        self.plan_used.pop(key, None)
+
+    def _evict_idle(self, need: int, keep) -> None:
+        """Destroys idle plans (no batch in flight), least recently used
+        first, until `need` more bytes fit the budget."""
+        idle = sorted((k for k in self.plan_bytes if k != keep and not self.plan_jobs.get(k)),
+                      key=lambda k: self.plan_used.get(k, -1))
+        for k in idle:
+            if self.resident_bytes() + self.in_use + need <= self.budget:
+                break
+            self._destroy_plan(k)
+            self.evictions += 1
+
+    def ensure_plan(self, shape, split: bool, cap: int = 0):
+        """The resident plan of (shape, precision), made for `cap` transforms
+        (default capacity) if missing."""
         key = (tuple(shape), split)
-        p = self.plans.get(key)
-        if p is None:
-            prec = TCFFT_FP16_SPLIT if split else TCFFT_FP16
-            cap = self.capacity(shape)
-            flags = TCFFT_PLAN_SHARE_SM if self.share_sm else 0
-            p = (Plan.plan_1d(shape[0], cap, prec, flags) if len(shape) == 1
-                 else Plan.plan_2d(shape[0], shape[1], cap, prec, flags))
+        if key not in self.plan_bytes:
+            cap = cap or self.capacity(shape, split)
+            p, nbytes = self._create_plan(tuple(shape), split, cap)
             self.plans[key] = p
-        return p
+            self.plan_bytes[key] = nbytes
+            self.plan_cap[key] = cap
+            self.plan_used.setdefault(key, -1)
+            self.peak_plan_bytes = max(self.peak_plan_bytes, sum(self.plan_bytes.values()))
+        return self.plans.get(key)
+
+    def plan(self, shape, split: bool) -> Plan:
+        return self.ensure_plan(shape, split)
 
     def prewarm(self, requests):
+        """Makes the plans of the trace's shapes while they fit in half the
+        budget (the others are made when first needed)."""
         for key in sorted({(r.shape, r.split) for r in requests}):
-            self.plan(*key)
+            cap = self.capacity(*key)
+            est = self.plan_estimate(key[0], key[1], cap)
+            if self.resident_bytes() + est <= self.budget // 2:
+                self.ensure_plan(key[0], key[1], cap)
         self.torch.cuda.synchronize()
+
+    def _admit(self, key, head, queue, inflight):
+        """Chooses the group for `key` (oldest request first) and the bytes it
+        needs, evicting idle plans or shrinking a new plan so that pool +
+        plans + batches in flight stay within the budget.  Returns (group,
+        job bytes) or None when the group has to wait."""
+        shape, split = key
+        m = int(np.prod(shape))
+        planes = 2 if split else 1
+        resident = key in self.plan_bytes
+        cap = self.capacity(shape, split)
+        plan_need = 0
+        if not resident:
+            # a new plan: halve its capacity while it cannot fit beside the
+            # head request (down to the head's own batch)
+            head_bytes = 2 * planes * head.points * 4
+            while True:
+                plan_need = self.plan_estimate(shape, split, cap)
+                room = self.budget - self.resident_bytes() - self.in_use
+                if plan_need + head_bytes <= room or cap <= head.batch:
+                    break
+                cap = max(head.batch, cap // 2)
+        group, total = [], 0
+        for r in queue:
+            if (r.shape, r.split) == key and total + r.batch <= cap:
+                group.append(r)
+                total += r.batch
+        nbytes = 2 * planes * total * m * 4
+        need = nbytes + plan_need
+        if self.resident_bytes() + self.in_use + need > self.budget:
+            self._evict_idle(need, keep=key)
+        if self.resident_bytes() + self.in_use + need > self.budget:
+            if not inflight:
+                raise RuntimeError("request larger than the HBM budget")
+            return None
+        if not resident:
+            self.ensure_plan(shape, split, cap)
+        return group, nbytes
 
     def assign_inputs(self, requests, seed: int = 6):
         rng = np.random.default_rng(seed)
@@ -173,6 +283,15 @@ class FFTServer:
     def run(self, requests, keep_outputs: bool = False, time_limit: float = 600.0):
         """Serve the trace in real time; returns statistics."""
         torch = self.torch
+        cuda = torch.cuda
+        # measured footprint: torch's allocations (pool, batch buffers; minus
+        # what the caller held before) plus the library's plan bytes, sampled
+        # after every launch (the only place either grows)
+        measure = hasattr(cuda, "memory_allocated")
+        base = (cuda.memory_allocated() - getattr(self, "pool_bytes", 0)) if measure else 0
+        device_peak = 0
+        self.peak_plan_bytes = sum(self.plan_bytes.values())
+        self.peak_in_use = self.resident_bytes()
         pending = deque(sorted(requests, key=lambda r: r.t_arrival))
         queue = deque()
         inflight = []
@@ -201,7 +320,10 @@ class FFTServer:
                         off += r.points
                     self.in_use -= job.nbytes
                     per_slot[job.stream_idx] -= 1
+                    self.plan_jobs[job.key] -= 1
+                    job.buffers = ()  # release the batch buffers now, as counted
                     inflight.remove(job)
+            job = None
             launched = False
             # start every job that has room: scan the queue in arrival order,
             # one group per (shape, precision); small and large jobs use their
@@ -217,11 +339,10 @@ class FFTServer:
                     if key in seen:
                         continue
                     seen.add(key)
-                    cap = self.capacity(head.shape)
-                    group, total = [], 0
+                    cap = self.capacity(head.shape, head.split)
+                    total = 0
                     for r in queue:
                         if (r.shape, r.split) == key and total + r.batch <= cap:
-                            group.append(r)
                             total += r.batch
                     pts = total * int(np.prod(head.shape))
                     pool = "small" if pts <= self.small_points else "large"
@@ -235,20 +356,24 @@ class FFTServer:
                     if not free:
                         blocked.add(pool)
                         continue
-                    planes = 2 if head.split else 1
-                    nbytes = 2 * planes * pts * 4
-                    if self.in_use + nbytes > self.budget:
-                        if not inflight:
-                            raise RuntimeError("request larger than the HBM budget")
+                    admitted = self._admit(key, head, queue, inflight)
+                    if admitted is None:
                         blocked.add(pool)  # admission: wait until running batches free memory
                         continue
+                    group, nbytes = admitted
                     for r in group:
                         queue.remove(r)
                     sidx = min(free, key=lambda i: per_slot[i])
-                    inflight.append(self._launch(group, key, sidx))
+                    job = self._launch(group, key, sidx)
+                    job.nbytes = nbytes
+                    inflight.append(job)
                     per_slot[sidx] += 1
+                    self.plan_jobs[key] = self.plan_jobs.get(key, 0) + 1
+                    self.plan_used[key] = batches
                     self.in_use += nbytes
-                    self.peak_in_use = max(self.peak_in_use, self.in_use)
+                    self.peak_in_use = max(self.peak_in_use, self.in_use + self.resident_bytes())
+                    if measure:
+                        device_peak = max(device_peak, cuda.memory_allocated() - base + sum(self.plan_bytes.values()))
                     batches += 1
                     launched = True
                     progressed = True
@@ -256,7 +381,10 @@ class FFTServer:
             if not launched and not (pending and pending[0].t_arrival <= time.perf_counter() - t0):
                 time.sleep(20e-6)
         torch.cuda.synchronize()
-        return self.stats(requests, batches)
+        out = self.stats(requests, batches)
+        if measure:
+            out["device_peak_bytes"] = int(device_peak)
+        return out
 
     def stats(self, requests, batches):
         lat = np.array([r.t_done - r.t_arrival for r in requests])
@@ -265,7 +393,8 @@ class FFTServer:
         out = {"requests": len(requests), "batches": batches,
                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                "mean_ms": float(lat.mean() * 1e3), "gflops": flops / span / 1e9, "span_s": span,
-               "peak_hbm_bytes": self.peak_in_use}
+               "peak_hbm_bytes": self.peak_in_use, "budget_bytes": self.budget,
+               "resident_bytes": self.resident_bytes(), "plan_evictions": self.evictions}
         # by request size: small requests stuck behind large ones show here
         for name, lo, hi in (("small", 0, 1 << 20), ("medium", 1 << 20, 1 << 24), ("large", 1 << 24, 1 << 62)):
             sel = [r for r in requests if lo <= r.points < hi]
@@ -284,6 +413,6 @@ class FFTServer:
         return out
 
     def close(self):
-        for p in self.plans.values():
-            p.destroy()
+        for k in list(self.plan_bytes):
+            self._destroy_plan(k)
         self.plans.clear()

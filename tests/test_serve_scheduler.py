@@ -38,12 +38,20 @@ class SimServer(FFTServer):
         self.depth = depth
         self.job_points = job_points
         self.plans = {}
+        self.plan_bytes, self.plan_cap, self.plan_used, self.plan_jobs = {}, {}, {}, {}
+        self.evictions = 0
+        self.pool_bytes = 0
         self.in_use = 0
         self.peak_in_use = 0
+        self.peak_plan_bytes = 0
+        self.footprints = []  # pool + plans + batches in flight, at every launch
         self.ns = ns_per_point
         self.log = []  # (launch time, stream, key, request ids, points)
         self.busy = [0] * len(self.slots)
         self.max_busy = [0] * len(self.slots)
+
+    def _create_plan(self, shape, split, cap):
+        return None, self.plan_estimate(shape, split, cap)  # no device: the estimate stands in
 
     def _launch(self, group, key, sidx):
         m = 1
@@ -51,6 +59,7 @@ class SimServer(FFTServer):
             m *= d
         pts = sum(r.batch for r in group) * m
         planes = 2 if key[1] else 1
+        self.footprints.append(self.resident_bytes() + self.in_use + 8 * planes * pts)
         self.log.append((time.perf_counter(), sidx, key, [r.rid for r in group], pts))
         self.busy[sidx] += 1
         self.max_busy[sidx] = max(self.max_busy[sidx], self.busy[sidx])
@@ -85,7 +94,7 @@ def test_pools_depth_and_merging():
     for _, sidx, key, ids, pts in srv.log:
         # a job is one (shape, precision) and at most the plan's capacity
         assert all((by_id[i].shape, by_id[i].split) == key for i in ids)
-        assert sum(by_id[i].batch for i in ids) <= srv.capacity(key[0])
+        assert sum(by_id[i].batch for i in ids) <= srv.capacity(key[0], key[1])
         # large jobs never take the small jobs' streams
         if pts > srv.small_points:
             assert sidx < srv.n_large
@@ -120,3 +129,30 @@ def test_request_larger_than_the_budget_is_refused():
     srv = SimServer(hbm_budget=1 << 20)
     with pytest.raises(RuntimeError, match="HBM budget"):
         srv.run([Request(0, 0.0, (1 << 14,), 64, True)], time_limit=10.0)
+
+
+def test_admission_counts_plans_and_pool_and_evicts_idle_plans():
+    # multi-pass 1D shapes whose plans hold a workspace: with the pool and the
+    # batches in flight they do not all fit, so idle plans are evicted (LRU)
+    # and the footprint at every launch stays within the budget
+    budget = 96 << 20
+    srv = SimServer(hbm_budget=budget, job_points=1 << 20)
+    srv.pool_bytes = 16 << 20
+    reqs = [Request(i, 0.0005 * i, (1 << (15 + i % 4),), 4, bool((i // 4) % 2)) for i in range(48)]
+    st = srv.run(reqs, time_limit=30.0)
+    assert st["requests"] == len(reqs) and all(r.t_done > 0 for r in reqs)
+    assert srv.evictions > 0 and st["plan_evictions"] == srv.evictions
+    assert max(srv.footprints) <= budget
+    assert 0 < srv.peak_in_use <= budget and srv.in_use == 0
+    assert st["resident_bytes"] == srv.resident_bytes() >= srv.pool_bytes
+
+
+def test_new_plan_shrinks_to_fit_the_budget():
+    # a plan whose default capacity cannot fit is made for fewer transforms
+    budget = 16 << 20  # the default 64-transform plan needs 16 MiB of workspace + tables
+    srv = SimServer(hbm_budget=budget, job_points=1 << 22)
+    reqs = [Request(i, 0.001 * i, (1 << 16,), 2, False) for i in range(6)]
+    st = srv.run(reqs, time_limit=30.0)
+    assert st["requests"] == 6
+    assert srv.plan_cap[((1 << 16,), False)] < max(64, (1 << 22) >> 16)
+    assert max(srv.footprints) <= budget
