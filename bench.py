@@ -55,8 +55,62 @@ def peaks():
 
 
 # ------------------------------------------------------------------ clocks
+class _NvmlPoller:
+    """Read-only NVML queries (SM clock, its maximum, power, clock-event
+    reasons) every `period` seconds from a thread, as nvidia-smi CSV lines.
+    NVML's poll rate keeps >= 10 samples inside a sub-second timed region,
+    where nvidia-smi's 200 ms loop records one or two."""
+
+    REASONS = ((0x8, "hw_slowdown"), (0x40, "hw_thermal_slowdown"), (0x20, "sw_thermal_slowdown"),
+               (0x4, "sw_power_cap"))
+
+    def __init__(self, gpu_index: int, period: float = 0.01):
+        import ctypes
+        import threading
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(gpu_index), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("no NVML handle")
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.gpu, self.period, self.lines = gpu_index, period, []
+        self.stop_ev = threading.Event()
+        self.th = threading.Thread(target=self._run, daemon=True)
+
+    def _line(self):
+        ct = self.ct
+        sm, smax, mw, mask = ct.c_uint(), ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(sm)) != 0:  # NVML_CLOCK_SM
+            return None
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ct.byref(smax))
+        self.lib.nvmlDeviceGetPowerUsage(self.h, ct.byref(mw))
+        self.reasons_fn(self.h, ct.byref(mask))
+        flags = ["Active" if mask.value & bit else "Not Active" for bit, _ in self.REASONS]
+        return ", ".join([str(self.gpu), str(sm.value), str(smax.value), f"{mw.value / 1000:.1f}",
+                          hex(mask.value)] + flags)
+
+    def _run(self):
+        while not self.stop_ev.is_set():
+            ln = self._line()
+            if ln:
+                self.lines.append(ln)
+            self.stop_ev.wait(self.period)
+
+    def start(self):
+        self.th.start()
+
+    def stop(self):
+        self.stop_ev.set()
+        self.th.join(timeout=2)
+        return list(self.lines)
+
+
 class ClockSampler:
-    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+    """Samples clocks and throttle reasons during the timed region: nvidia-smi
+    (200 ms loop) plus NVML polling every 10 ms where libnvidia-ml loads."""
 
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -71,6 +125,12 @@ class ClockSampler:
         self.path = os.path.join(d, f"clocks_gpu{gpu_index}.csv")
 
     def start(self):
+        self.nvml = None
+        try:
+            self.nvml = _NvmlPoller(self.gpu)
+            self.nvml.start()
+        except Exception:
+            self.nvml = None
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
@@ -81,29 +141,36 @@ class ClockSampler:
             self.proc = None
 
     def stop(self):
-        if self.proc is None:
+        extra = self.nvml.stop() if getattr(self, "nvml", None) is not None else []
+        if self.proc is None and not extra:
             return None
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        self.f.close()
+        lines = list(extra)
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+            with open(self.path) as f:
+                lines += f.readlines()
+            if extra:  # keep the NVML samples beside nvidia-smi's
+                with open(self.path, "a") as f:
+                    f.write("\n".join(extra) + "\n")
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        with open(self.path) as f:
-            for line in f:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) < 9:
-                    continue
-                try:
-                    sm.append(float(parts[1]))
-                    smax = float(parts[2])
-                except ValueError:
-                    continue
-                for nm, v in zip(names, parts[5:9]):
-                    if v.lower() == "active":
-                        reasons.add(nm)
+        for line in lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
@@ -274,62 +341,80 @@ def _split_draw(n_values: int, seed: int):
 DTYPES = {"fp16": "f16", "split": "f16 split (hi+lo, 3 products)", "fp32": "f32 io, f16 split (3 products)"}
 
 
-def _f32_draw(n_values: int, seed: int):
-    """n_values FP32 numbers uniform in [-1, 1] (re/im interleaved when used as complex)."""
+def _fast_uniform(n_values: int, seed: int, dtype):
+    """n_values numbers uniform in [-1, 1) from a seeded FP32 draw, cast to dtype."""
     import numpy as np
     rng = np.random.default_rng(seed)
-    return rng.uniform(-1.0, 1.0, size=n_values).astype(np.float32)
+    v = rng.random(n_values, dtype=np.float32)
+    v *= 2.0
+    v -= 1.0
+    return v.astype(dtype)
 
 
 def build_sweep(args, dev, rank):
-    """The 1D sweep: one exec per N = 2^8..2^24 over the same 2^28-point buffers,
+    """The 1D sweep: one exec per N = 2^8..2^24 over 2^28-point buffers, each
+    size with its own seeded input (seed 1000 + log2 N, plus 100 per rank),
     in plain FP16 (the benchmark), split FP16 or FP32 in and out."""
     import numpy as np
     import torch
     import paper_2104_11471_gb300 as tc
+    import seeded_inputs as si
     sizes = [int(s) for s in args.sizes.split(",")] if args.sizes else SWEEP
     prec = args.precision
-    lo = None
     if prec == "fp32":
-        h = _f32_draw(2 * POINTS, 1000 + rank)
-        x = torch.from_numpy(h).to(dev)
         code, bpp, label = tc.TCFFT_FP32, 16.0, "FP32 complex in and out (split FP16 tensor-core stages)"
     elif prec == "split":
-        h, lo = _split_draw(2 * POINTS, 1000 + rank)
-        x = torch.from_numpy(np.concatenate([h, lo]).view(np.uint16)).to(dev)
         code, bpp, label = tc.TCFFT_FP16_SPLIT, 16.0, "split FP16 (hi + 2^-11 lo planes)"
     else:
-        h = _half_draw(2 * POINTS, 1000 + rank)
-        x = torch.from_numpy(h.view(np.uint16)).to(dev)
         code, bpp, label = tc.TCFFT_FP16, 8.0, "plain FP16"
-    y = torch.empty_like(x)
+    y = None
     entries = []
+    host = (None, None)
     for lg in sizes:
         n = 1 << lg
         b = POINTS // n
+        seed = si.sweep_seed(lg) + 100 * rank
+        lo = None
+        if prec == "fp32":
+            h = _fast_uniform(2 * POINTS, seed, np.float32)
+            x = torch.from_numpy(h).to(dev)
+        elif prec == "split":
+            v = _fast_uniform(2 * POINTS, seed, np.float64)
+            h = v.astype(np.float16)
+            lo = ((v - h.astype(np.float64)) * 2048.0).astype(np.float16)
+            del v
+            x = torch.from_numpy(np.concatenate([h, lo]).view(np.uint16)).to(dev)
+        else:
+            h = _fast_uniform(2 * POINTS, seed, np.float16)
+            x = torch.from_numpy(h.view(np.uint16)).to(dev)
+        if y is None:
+            y = torch.empty_like(x)
+        host = (h, lo)
         plan = tc.Plan.plan_1d(n, b, code, 0 if args.no_autotune else tc.TCFFT_PLAN_AUTOTUNE)
+        row = b // 2  # one transform from the middle of the batch
+        sl = slice(row * 2 * n, (row + 1) * 2 * n)
+        xin = h[sl].astype(np.float64)
+        if prec == "split":
+            xin = xin + lo[sl].astype(np.float64) / 2048.0
 
-        def check(orc, y=y, n=n, b=b):
-            row = b // 2  # one transform from the middle of the batch
-            sl = slice(row * 2 * n, (row + 1) * 2 * n)
-            xin = h[sl].astype(np.float64)
+        def check(orc, y=y, n=n, sl=sl, xin=xin):
             if prec == "fp32":
                 out = y[sl].cpu().numpy().astype(np.float64)
             else:
                 out = y[sl].cpu().numpy().view(np.float16).astype(np.float64)
             if prec == "split":
-                xin = xin + lo[sl].astype(np.float64) / 2048.0
                 out = out + y[2 * POINTS:][sl].cpu().numpy().view(np.float16).astype(np.float64) / 2048.0
             ref = orc.fft_batch((xin[0::2] + 1j * xin[1::2])[None, :])[0]
             return orc.rel_l2(out[0::2] + 1j * out[1::2], ref)
+
         entries.append(Entry(f"1d n={n} batch={b}", plan, x, y, flops_1d(n, b), bpp * n * b, check))
     cfg = {"workload": f"1d_sweep: N=2^8..2^24 step 2^2, batch=2^{args.log2_points}/N, "
-                       "one exec per size per step, uniform[-1,1] seeded inputs",
+                       "one exec per size per step, uniform[-1,1] inputs seeded per size (1000 + log2 N)",
            "sizes": [1 << s for s in sizes], "points_per_exec": POINTS, "precision": label,
            "geometry": "fixed planner" if args.no_autotune else "plan-time autotuner (not timed)",
            "l2": "inputs larger than L2 (1 GiB per exec), no flush"}
     cpu_sizes = [(1 << s,) for s in sizes]
-    return entries, cfg, cpu_sizes, (h, lo)
+    return entries, cfg, cpu_sizes, host
 
 
 def build_2d(args, dev, rank):
@@ -486,6 +571,8 @@ def run_serve(args, world, rank, local):
                    "parallelism": f"replicas x{world}"},
         "serve": {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
                   "requests": st["requests"], "batches": st["batches"], "peak_hbm_bytes": st["peak_hbm_bytes"],
+                  "device_peak_bytes": st.get("device_peak_bytes"), "resident_bytes": st.get("resident_bytes"),
+                  "budget_bytes": st.get("budget_bytes"), "plan_evictions": st.get("plan_evictions"),
                   "plain": st.get("plain"), "split": st.get("split"),
                   "by_size": {k: st[k] for k in ("small_points", "medium_points", "large_points") if k in st}},
         "roofline": {"bound": "hbm", "achieved": round(alg / span / 1e9, 1), "peak": peak, "unit": "GB/s",
