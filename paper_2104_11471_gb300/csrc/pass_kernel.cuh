@@ -634,16 +634,18 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
 
     if (p.async_load) {
       if (K::IN_C || p.in_tma) {
-        const bool got = mbar_wait_bounded(lbar_s, lphase, kWaitLimitCycles);
-        if (got) {
-          lphase ^= 1u;
-          pending = false;
-        }
+        // one thread polls the copy's barrier; the others sleep in the CTA
+        // barrier (no issue slots spent spinning) and see the copied bytes
+        // through it
+        bool got = true;
+        if (tid == 0) got = mbar_wait_bounded(lbar_s, lphase, kWaitLimitCycles);
         if (__syncthreads_or(!got)) {
           if (tid == 0) atomicExch(p.status, kDevErrTimeout);
           ok = false;
           break;
         }
+        lphase ^= 1u;
+        pending = false;
       } else {
         cp_async_wait_all();
         __syncthreads();
@@ -697,8 +699,12 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
         }
         mma_commit(mbar_s);
       }
-      const bool got = mbar_wait_bounded(mbar_s, phase, kWaitLimitCycles);
+      // the issuing thread polls the MMA barrier; the others sleep in the
+      // CTA barrier, ordered after the MMAs by the tcgen05 fence pair
+      bool got = true;
+      if (tid == 0) got = mbar_wait_bounded(mbar_s, phase, kWaitLimitCycles);
       phase ^= 1u;
+      tc_fence_before_sync();
       if (__syncthreads_or(!got)) {
         if (tid == 0) atomicExch(p.status, kDevErrTimeout);
         ok = false;
