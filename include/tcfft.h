@@ -88,6 +88,17 @@ typedef enum {
                                   that kernels on other (higher-priority)
                                   streams find room while this plan runs
                                   (serving: large jobs beside small ones) */
+#define TCFFT_PLAN_FUSED_2D 32u /* square 2D transforms up to 512 x 512 (256 x
+                                  256 split; ragged groups too): rows and
+                                  columns in one launch, a cluster of up to 16
+                                  CTAs per matrix exchanging the row results
+                                  through distributed shared memory, one HBM
+                                  read and one write per matrix (Sec. 3.1, 2D
+                                  FFT).  Off by default: on GB300 the stage
+                                  kernels are bound by on-chip work, not HBM,
+                                  and the two-pass plan is faster; with
+                                  TCFFT_PLAN_AUTOTUNE the faster of the two is
+                                  timed and kept */
 
 /* Plan a batch of `batch` 1D transforms of length n (the paper's
  * tcfftPlan1D(plan, nx, batch), Sec. 3.1).  Allocates device twiddle tables

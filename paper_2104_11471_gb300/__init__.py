@@ -27,6 +27,7 @@ TCFFT_PLAN_GRAPH = 2
 TCFFT_PLAN_INVERSE = 4
 TCFFT_PLAN_SCALE = 8
 TCFFT_PLAN_SHARE_SM = 16  # at most half of each SM's CTA slots (room for other streams)
+TCFFT_PLAN_FUSED_2D = 32  # square 2D up to 512^2: rows and columns in one cluster launch
 
 STATUS = {
     0: "TCFFT_OK", 1: "TCFFT_ERR_INVALID_SIZE", 2: "TCFFT_ERR_INVALID_VALUE",

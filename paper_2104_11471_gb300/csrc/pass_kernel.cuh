@@ -536,6 +536,352 @@ __device__ __forceinline__ RowChunks row_chunks(uint32_t m0, uint32_t k) {
   return r;
 }
 
+// Final-stage outputs of one butterfly into the natural-order staging copy
+// at A (P points per plane): word c*N + k (contiguous output) or k*C + c
+// (strided output), XORed with the bank-spreading key, or with the tensor
+// map's swizzle when the chunk leaves through tensor-map stores.
+template <class K>
+__device__ __forceinline__ void staging_store(const PassParams& p, uint8_t* A, uint32_t P, int log2C, uint32_t c,
+                                              uint32_t kbase, const float2 (&X)[8], const float2 (&Y)[8]) {
+  constexpr uint32_t kstep = (uint32_t)K::LQ << K::LOG2RX;  // output index step per k_S
+  uint32_t* stg = reinterpret_cast<uint32_t*>(A);
+  const uint32_t base = K::OUT_C ? ((c << K::LOG2N) + kbase) : ((kbase << log2C) + c);
+  // bank-spreading key; for tensor-map stores the map's swizzle (the
+  // 16-byte chunk index XOR the 128-byte line index, over rows of
+  // C * 4 bytes), which is constant over a thread's 16 words here
+  uint32_t key = stg_key<K>(c, kbase, log2C) << 2;
+  if constexpr (K::OUT_C) {
+    if (K::S == 3 && p.out_tma) key = ((base >> 5) & 7u) << 2;  // rows of 32 points
+  } else {
+    if (p.out_tma) key = ((base >> 5) & ((1u << (log2C - 2)) - 1u)) << 2;
+  }
+  const uint32_t wstep = K::OUT_C ? kstep : (kstep << log2C);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const uint32_t i0 = (base + (2 * i) * wstep) ^ key;
+    const uint32_t i1 = (base + (2 * i + 1) * wstep) ^ key;
+    if (K::SPLIT && p.out_f32) {
+      // FP32 output: the two staging planes hold re and im
+      stg[i0] = __float_as_uint(X[i].x);
+      stg[i1] = __float_as_uint(X[i].y);
+      stg[P + i0] = __float_as_uint(Y[i].x);
+      stg[P + i1] = __float_as_uint(Y[i].y);
+      continue;
+    }
+    const uint32_t h0 = f2h2(X[i].x, Y[i].x), h1 = f2h2(X[i].y, Y[i].y);
+    stg[i0] = h0;
+    stg[i1] = h1;
+    if constexpr (K::SPLIT) {
+      stg[P + i0] = split_lo(X[i].x, Y[i].x, h0);
+      stg[P + i1] = split_lo(X[i].y, Y[i].y, h1);
+    }
+  }
+}
+
+// Staging copy (natural order, chunk-swizzled, at A) -> global memory for
+// the chunk of transforms t0 .. t0 + nvalid - 1 whose output starts at gout:
+// tensor-map stores issued by one thread (which waits until they have read
+// the staging copy) or 16-byte stores by every thread.
+template <class K>
+__device__ __forceinline__ void copy_out(const PassParams& p, uint8_t* A, uint32_t* gout, int64_t t0, int nvalid,
+                                         int log2C) {
+  const int tid = threadIdx.x;
+  const uint32_t P = (uint32_t)1 << (log2C + K::LOG2N);
+  const uint32_t ow = out_words<K>(p);
+  const uint4* stg = reinterpret_cast<const uint4*>(A);
+  const uint32_t nch = P >> 2;
+  if (K::OUT_C && K::S == 3 && p.out_tma) {
+    // rows of 32 points in the 128-byte swizzle, up to 256 rows per box;
+    // rows past the end of the output are not written
+    if (tid == 0) {
+      const int row0 = (int)((gout - p.out) >> 5);
+      const uint32_t a0 = smem_u32(A);
+      for (int pl = 0; pl < K::PLANES; ++pl)
+        for (uint32_t r0 = 0; r0 < (P >> 5); r0 += 256)
+          tma_store_5d(&p.out_map, a0 + (uint32_t)pl * (P * 4u) + r0 * 128u, 0, row0 + (int)r0, pl, 0, 0);
+      bulk_commit();
+      bulk_wait_read();  // the staging copy (= A) is rewritten by the next chunk
+    }
+  } else if constexpr (K::OUT_C) {
+    const uint32_t vchunks = ((uint32_t)nvalid << K::LOG2N) >> 2;
+    for (uint32_t q = tid; q < vchunks; q += blockDim.x) {
+      const uint32_t c = (q << 2) >> K::LOG2N;
+      const uint32_t ko = (q << 2) & (K::N - 1);
+      const uint32_t pq = q ^ stg_key<K>(c, ko, log2C);
+      uint32_t* o = p.out_scatter ? p.out + ow * (side_base(p.out_l, t0 + c, p.log2I1, p.log2I2) + ko)
+                                  : gout + ow * (q << 2);
+      if (K::SPLIT && p.out_f32) {
+        // four points: re and im planes -> interleaved FP32 complex
+        const uint4 re = stg[pq], im = stg[nch + pq];
+        reinterpret_cast<uint4*>(o)[0] = make_uint4(re.x, im.x, re.y, im.y);
+        reinterpret_cast<uint4*>(o)[1] = make_uint4(re.z, im.z, re.w, im.w);
+        continue;
+      }
+      *reinterpret_cast<uint4*>(o) = stg[pq];
+      if constexpr (K::SPLIT) *reinterpret_cast<uint4*>(o + p.out_plane) = stg[nch + pq];
+    }
+  } else if (p.out_tma) {
+    // tensor-map boxes of C columns x 256 elements per plane, one thread
+    if (tid == 0) {
+      const int64_t t1 = t0 & ((int64_t(1) << p.log2I1) - 1);
+      const int64_t t23 = t0 >> p.log2I1;
+      const int t2 = (int)(t23 & ((int64_t(1) << p.log2I2) - 1));
+      const int t3 = (int)(t23 >> p.log2I2);
+      const uint32_t a0 = smem_u32(A);
+      for (int pl = 0; pl < K::PLANES; ++pl)
+        for (int e0 = 0; e0 < K::N; e0 += 256)
+          tma_store_5d(&p.out_map, a0 + (uint32_t)pl * (P * 4u) + ((uint32_t)e0 << log2C) * 4u, (int)t1, e0,
+                       t2, t3, pl);
+      bulk_commit();
+      bulk_wait_read();  // the staging copy (= A) is rewritten by the next chunk
+    }
+  } else {
+    const int cq = log2C - 2;  // log2 of the chunks per output element index
+    const uint32_t es = p.out_l.es;
+    for (uint32_t q = tid; q < nch; q += blockDim.x) {
+      const uint32_t ko = q >> cq;
+      const uint32_t cc = (q & ((1u << cq) - 1u)) << 2;
+      const uint32_t off = ko * es + cc;
+      const uint32_t pq = q ^ stg_key<K>(cc, ko, log2C);
+      if (K::SPLIT && p.out_f32) {
+        const uint4 re = stg[pq], im = stg[nch + pq];
+        uint4* o = reinterpret_cast<uint4*>(gout + 2u * off);
+        o[0] = make_uint4(re.x, im.x, re.y, im.y);
+        o[1] = make_uint4(re.z, im.z, re.w, im.w);
+        continue;
+      }
+      *reinterpret_cast<uint4*>(gout + off) = stg[pq];
+      if constexpr (K::SPLIT) *reinterpret_cast<uint4*>(gout + p.out_plane + off) = stg[nch + pq];
+    }
+  }
+}
+
+// DFT matrix images -> shared memory at Bs (the global table holds 8 hi then
+// 8 lo images): plain, hi image k0 in slot k0; split, hi image k0 in slot 2 k0
+// and its lo image in slot 2 k0 + 1, so that [B_hi | B_lo] is one N = 64
+// operand.  FOLD kernels take one image per leading-radix digit k0.
+template <class K>
+__device__ __forceinline__ void load_dft_images(const PassParams& p, uint8_t* Bs) {
+  constexpr int NB = K::FOLD ? K::RX : 1;
+  const uint4* src = reinterpret_cast<const uint4*>(p.dft_b);
+  uint4* dst = reinterpret_cast<uint4*>(Bs);
+  constexpr int per = kBImageBytes / 16;
+  for (int i = threadIdx.x; i < K::PLANES * NB * per; i += (int)blockDim.x) {
+    const int slot = i / per, r = i - slot * per;
+    const int plane = K::SPLIT ? (slot & 1) : 0, k0 = K::SPLIT ? (slot >> 1) : slot;
+    dst[i] = __ldg(src + (plane * 8 + k0) * per + r);
+  }
+}
+
+// ------------------------------------------------------------ stage loop
+// The S radix-16 stages of one chunk whose stage-1 A operand is in shared
+// memory: per stage, one thread issues the MMAs of every tile (stage 1 with
+// FOLD: the DFT image of the tile's k0) and commits them to the MMA barrier;
+// the epilogue warps read the accumulators, apply the stage twiddle and write
+// the next stage's A in place.  After the last stage each butterfly's 16
+// outputs go to fin(c, kbase, X, Y): transform c of the chunk, output index
+// kbase + (2i) kstep in X[i].x / Y[i].x (re / im) and kbase + (2i+1) kstep in
+// X[i].y / Y[i].y, kstep = 16^{S-1} R.  Returns false (status written) when
+// an MMA wait times out.
+struct StageCtx {
+  uint8_t* A;       // stage operand tiles (1 KB aligned); split: lo plane follows
+  uint32_t a_base;  // shared-memory address of A
+  uint32_t b_base;  // shared-memory address of the DFT-matrix images
+  uint32_t tmem;    // TMEM base address
+  uint32_t mbar_s;  // MMA completion barrier
+  uint32_t phase;   // its current parity
+};
+
+template <class K, class Final>
+__device__ __forceinline__ bool run_stages(const PassParams& p, StageCtx& cx, int tiles, int log2C, Final& fin) {
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int quarter = warp & 3;  // TMEM lane quarter of this warp
+  const int half = warp >> 2;    // which tiles this warp takes in the epilogue
+  const int halves = (int)(blockDim.x >> 7);  // warps per TMEM lane quarter
+  const uint32_t rows_valid = (uint32_t)1 << (log2C + K::LOG2N - 4);  // butterflies per stage
+  const uint32_t idesc = make_idesc_f16(128, 32, 1, 0);
+  const uint32_t idesc64 = make_idesc_f16(128, 64, 1, 0);  // split: [B_hi | B_lo]
+  uint8_t* A = cx.A;
+  const uint32_t a_base = cx.a_base, b_base = cx.b_base, tmem = cx.tmem, mbar_s = cx.mbar_s;
+  uint32_t& phase = cx.phase;
+#pragma unroll
+  for (int j = 1; j <= K::S; ++j) {
+    if (tid == 0) {
+      tc_fence_after_sync();
+      for (int t = 0; t < tiles; ++t) {
+        const uint32_t a = a_base + t * kTileBytes;
+        // stage 1 with FOLD: the DFT matrix of this tile's k0
+        const uint32_t kb = (K::FOLD && j == 1) ? ((uint32_t)(t * 128) >> (log2C + K::LOG2LQ)) : 0u;
+        if constexpr (!K::SPLIT) {
+          const uint32_t d = tmem + 32u * t;
+          const uint32_t bb = b_base + kb * kBImageBytes;
+          mma_f16(d, make_smem_desc(a, 4096, 1024, 2), make_smem_desc(bb, 128, 512, 0), idesc, 0);
+          mma_f16(d, make_smem_desc(a + 2048, 4096, 1024, 2),
+                  make_smem_desc(bb + 256, 128, 512, 0), idesc, 1);
+        } else {
+          // tile t owns TMEM columns [64 t, 64 t + 64): the main product
+          // A_hi B_hi in the first 32, the correction A_hi B_lo + A_lo B_hi in
+          // the second.  One N = 64 MMA forms A_hi [B_hi | B_lo] (the lo image
+          // follows its hi image, at the same 512-byte group stride), one
+          // N = 32 MMA adds A_lo B_hi; per K half.
+          const uint32_t dm = tmem + 64u * t;
+          const uint32_t bb = b_base + 2u * kb * kBImageBytes;
+          const uint32_t alo = a + tiles * kTileBytes;
+          mma_f16(dm, make_smem_desc(a, 4096, 1024, 2), make_smem_desc(bb, 128, 512, 0), idesc64, 0);
+          mma_f16(dm + 32u, make_smem_desc(alo, 4096, 1024, 2), make_smem_desc(bb, 128, 512, 0), idesc, 1);
+          mma_f16(dm, make_smem_desc(a + 2048, 4096, 1024, 2), make_smem_desc(bb + 256, 128, 512, 0),
+                  idesc64, 1);
+          mma_f16(dm + 32u, make_smem_desc(alo + 2048, 4096, 1024, 2),
+                  make_smem_desc(bb + 256, 128, 512, 0), idesc, 1);
+        }
+      }
+      mma_commit(mbar_s);
+    }
+    // the issuing thread polls the MMA barrier; the others sleep in the
+    // CTA barrier, ordered after the MMAs by the tcgen05 fence pair
+    bool got = true;
+    if (tid == 0) got = mbar_wait_bounded(mbar_s, phase, kWaitLimitCycles);
+    phase ^= 1u;
+    tc_fence_before_sync();
+    if (__syncthreads_or(!got)) {
+      if (tid == 0) atomicExch(p.status, kDevErrTimeout);
+      return false;
+    }
+    tc_fence_after_sync();
+
+    const bool last = (j == K::S);
+    for (int t = half; t < tiles; t += halves) {
+      const uint32_t row = rp((uint32_t)t * 128u + 32u * quarter + lane);  // logical row of this lane
+      // X[i] = (Re out 2i, Re out 2i+1), Y[i] = (Im out 2i, Im out 2i+1)
+      float2 X[8], Y[8];
+      {
+        const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (K::SPLIT ? 64u : 32u) * t;
+        float v[32];
+        tmem_ld32_wait(taddr, v);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          X[i] = make_float2(v[2 * i], v[2 * i + 1]);
+          Y[i] = make_float2(v[16 + 2 * i], v[16 + 2 * i + 1]);
+        }
+        if constexpr (K::SPLIT) {
+          tmem_ld32_wait(taddr + 32u, v);
+          const float2 s = make_float2(1.0f / 2048.0f, 1.0f / 2048.0f);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            X[i] = __ffma2_rn(make_float2(v[2 * i], v[2 * i + 1]), s, X[i]);
+            Y[i] = __ffma2_rn(make_float2(v[16 + 2 * i], v[16 + 2 * i + 1]), s, Y[i]);
+          }
+        }
+      }
+      if (row >= rows_valid) continue;  // padding rows of a partial last tile
+
+      // butterfly identity of this row at stage j: sub-transform g, the
+      // digits kk = (k_1 .. k_{j-1}) already produced, and nrest = n^(j+1)
+      uint32_t g, nrest, kk;
+      uint32_t k0row = 0;  // k0 of the row (stage 1)
+      if (j == 1) {
+        kk = 0;
+        const uint32_t lk = (uint32_t)log2C + K::LOG2LQ;  // rows per k0
+        k0row = row >> lk;
+        const uint32_t rem = row & ((1u << lk) - 1u);
+        uint32_t c1;
+        if constexpr (K::IN_C) {
+          c1 = rem >> K::LOG2LQ;
+          nrest = rem & (K::LQ - 1);
+        } else {
+          nrest = rem >> log2C;
+          c1 = rem & ((1u << log2C) - 1u);
+        }
+        g = (k0row << log2C) + c1;
+      } else {
+        const int sj = 4 * (j - 1);
+        kk = row & ((1u << sj) - 1u);
+        const uint32_t q = row >> sj;
+        const int sr = 4 * (K::S - j);
+        g = q >> sr;
+        nrest = q & ((1u << sr) - 1u);
+      }
+
+      if (!last) {
+        // twiddle of output k: a b^k with (a, b) from the stage table:
+        // stage 1: a = W_N^{k0 nrest}, b = W_{L}^{nrest}; stage j >= 2:
+        // a = 1, b = W_{L_j}^{nrest}.  Pairs (a b^{2i}, a b^{2i+1}) are
+        // advanced by b^2 in packed FP32x2 arithmetic.
+        {
+          int toff = 0;
+          if (j >= 2) toff = K::RX << K::LOG2LQ;
+#pragma unroll
+          for (int i = 2; i < j; ++i) toff += 1 << (4 * (K::S - i));
+          const int ent = toff + (j == 1 ? (int)((k0row << K::LOG2LQ) + nrest) : (int)nrest);
+          const float4 e = __ldg(p.stw + ent);
+          const float2 a = make_float2(e.x, e.y), b = make_float2(e.z, e.w);
+          const float2 ab = cmulf(a, b), b2 = cmulf(b, b);
+          float2 c2 = make_float2(a.x, ab.x), d2 = make_float2(a.y, ab.y);
+          const float2 sc = make_float2(b2.x, b2.x), sd = make_float2(b2.y, b2.y);
+          const float2 snd = make_float2(-b2.y, -b2.y);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            cmul2(X[i], Y[i], c2, d2, make_float2(-d2.x, -d2.y));
+            if (i < 7) {
+              float2 cn = c2, dn = d2;
+              cmul2(cn, dn, sc, sd, snd);
+              c2 = cn;
+              d2 = dn;
+            }
+          }
+        }
+        const int sh = 4 * (K::S - j - 1);
+        const uint32_t nnext = nrest >> sh;
+        const uint32_t nlow = nrest & ((1u << sh) - 1u);
+        const uint32_t dr = ((((g << sh) + nlow) << (4 * j)) + (kk << 4));
+        const RowChunks rc = row_chunks(dr, nnext);
+        uint32_t hr[8], hi[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          hr[i] = f2h2(X[i].x, X[i].y);
+          hi[i] = f2h2(Y[i].x, Y[i].y);
+        }
+        *reinterpret_cast<uint4*>(A + rc.re0) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+        *reinterpret_cast<uint4*>(A + rc.re0 + 2048) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(A + rc.re1) = make_uint4(hr[4], hr[5], hr[6], hr[7]);
+        *reinterpret_cast<uint4*>(A + rc.re1 + 2048) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+        if constexpr (K::SPLIT) {
+          uint32_t lr[8], li[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            lr[i] = split_lo(X[i].x, X[i].y, hr[i]);
+            li[i] = split_lo(Y[i].x, Y[i].y, hi[i]);
+          }
+          uint8_t* Alo = A + tiles * kTileBytes;
+          *reinterpret_cast<uint4*>(Alo + rc.re0) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
+          *reinterpret_cast<uint4*>(Alo + rc.re0 + 2048) = make_uint4(li[0], li[1], li[2], li[3]);
+          *reinterpret_cast<uint4*>(Alo + rc.re1) = make_uint4(lr[4], lr[5], lr[6], lr[7]);
+          *reinterpret_cast<uint4*>(Alo + rc.re1 + 2048) = make_uint4(li[4], li[5], li[6], li[7]);
+        }
+      } else {
+        // final stage: the output identity of this butterfly
+        uint32_t rev = 0;
+        {
+          uint32_t x = kk;
+#pragma unroll
+          for (int d = 0; d < K::S - 1; ++d) {
+            rev = (rev << 4) | (x & 15u);
+            x >>= 4;
+          }
+        }
+        const uint32_t k0 = g >> log2C;
+        const uint32_t c = g & ((1u << log2C) - 1u);
+        fin(c, k0 + (rev << K::LOG2RX), X, Y);
+      }
+    }
+    fence_proxy_async_smem();
+    tc_fence_before_sync();
+    __syncthreads();
+  }
+  return true;
+}
+
 // ---------------------------------------------------------------- kernel
 // Persistent: CTA b processes chunks b, b + gridDim.x, ... (C transforms
 // each).  With async_load, the raw input of the next chunk is copied into
@@ -564,24 +910,9 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
 
   const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
-  const int quarter = warp & 3;  // TMEM lane quarter of this warp
-  const int half = warp >> 2;    // which tiles this warp takes in the epilogue
-  const int halves = (int)(blockDim.x >> 7);  // warps per TMEM lane quarter
+  const int warp = tid >> 5;
 
-  // DFT matrix images -> shared memory (the global table holds 8 hi then 8 lo
-  // images): plain, hi image k0 in slot k0; split, hi image k0 in slot 2 k0 and
-  // its lo image in slot 2 k0 + 1, so that [B_hi | B_lo] is one N = 64 operand.
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(p.dft_b);
-    uint4* dst = reinterpret_cast<uint4*>(Bs);
-    constexpr int per = kBImageBytes / 16;
-    for (int i = tid; i < K::PLANES * NB * per; i += (int)blockDim.x) {
-      const int slot = i / per, r = i - slot * per;
-      const int plane = K::SPLIT ? (slot & 1) : 0, k0 = K::SPLIT ? (slot >> 1) : slot;
-      dst[i] = __ldg(src + (plane * 8 + k0) * per + r);
-    }
-  }
+  load_dft_images<K>(p, Bs);
   if (tid == 0) {
     mbar_init(smem_u32(mbar), 1);
     mbar_init(smem_u32(lbar), 1);
@@ -592,13 +923,10 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
     tmem_relinquish();
   }
 
-  const uint32_t rows_valid = (uint32_t)C << (LOG2N - 4);  // butterflies per stage
-  const uint32_t idesc = make_idesc_f16(128, 32, 1, 0);
-  const uint32_t idesc64 = make_idesc_f16(128, 64, 1, 0);  // split: [B_hi | B_lo]
-  const uint32_t a_base = smem_u32(A), b_base = smem_u32(Bs), raw_s = smem_u32(RAW);
-  const uint32_t mbar_s = smem_u32(mbar), lbar_s = smem_u32(lbar);
+  const uint32_t raw_s = smem_u32(RAW);
+  const uint32_t lbar_s = smem_u32(lbar);
   const uint32_t* raw32 = reinterpret_cast<const uint32_t*>(RAW);
-  uint32_t phase = 0, lphase = 0;
+  uint32_t lphase = 0;
   bool ok = true, pending = false;  // pending: a bulk copy into RAW is in flight
 
   auto chunk_in = [&](int64_t ch) {
@@ -613,6 +941,7 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
   __syncthreads();  // barriers initialised, TMEM address published
   tc_fence_after_sync();
   const uint32_t tmem = *tslot;
+  StageCtx cx{A, smem_u32(A), smem_u32(Bs), tmem, smem_u32(mbar), 0u};
 
   // everything above reads only plan-time tables; the pass input may be the
   // previous kernel's output
@@ -666,342 +995,73 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
     tc_fence_before_sync();
     __syncthreads();
 
+    // final stage: transform c of the chunk, output index kbase at k_S = 0
+    auto fin = [&](uint32_t c, uint32_t kbase, float2 (&X)[8], float2 (&Y)[8]) {
+      constexpr uint32_t kstep = (uint32_t)K::LQ << K::LOG2RX;  // output index step per k_S
+      if (p.otw_level) {
+        // W_M^{col (kbase + kstep k)}: powers of ws = W_M^{col kstep} from
+        // w0 = W_M^{col kbase}, advanced two outputs at a time
+        const int64_t t = t0 + c;
+        const uint32_t col = (p.otw_level == 1)
+                                 ? (uint32_t)(t & ((int64_t(1) << p.log2I1) - 1))
+                                 : (uint32_t)((t >> p.log2I1) & ((int64_t(1) << p.log2I2) - 1));
+        const float2 w0 = tw_lookup(p.otw_lo, p.otw_hi, col * kbase, p.otw_log2M, p.otw_log2S);
+        const float2 ws = tw_lookup(p.otw_lo, p.otw_hi, col * kstep, p.otw_log2M, p.otw_log2S);
+        const float2 w1 = cmulf(w0, ws), ws2 = cmulf(ws, ws);
+        float2 c2 = make_float2(w0.x, w1.x), d2 = make_float2(w0.y, w1.y);
+        const float2 sc = make_float2(ws2.x, ws2.x), sd = make_float2(ws2.y, ws2.y);
+        const float2 snd = make_float2(-ws2.y, -ws2.y);
 #pragma unroll
-    for (int j = 1; j <= K::S; ++j) {
-      if (tid == 0) {
-        tc_fence_after_sync();
-        for (int t = 0; t < tiles; ++t) {
-          const uint32_t a = a_base + t * kTileBytes;
-          // stage 1 with FOLD: the DFT matrix of this tile's k0
-          const uint32_t kb = (K::FOLD && j == 1) ? ((uint32_t)(t * 128) >> (log2C + K::LOG2LQ)) : 0u;
-          if constexpr (!SPLIT) {
-            const uint32_t d = tmem + 32u * t;
-            const uint32_t bb = b_base + kb * kBImageBytes;
-            mma_f16(d, make_smem_desc(a, 4096, 1024, 2), make_smem_desc(bb, 128, 512, 0), idesc, 0);
-            mma_f16(d, make_smem_desc(a + 2048, 4096, 1024, 2),
-                    make_smem_desc(bb + 256, 128, 512, 0), idesc, 1);
-          } else {
-            // tile t owns TMEM columns [64 t, 64 t + 64): the main product
-            // A_hi B_hi in the first 32, the correction A_hi B_lo + A_lo B_hi in
-            // the second.  One N = 64 MMA forms A_hi [B_hi | B_lo] (the lo image
-            // follows its hi image, at the same 512-byte group stride), one
-            // N = 32 MMA adds A_lo B_hi; per K half.
-            const uint32_t dm = tmem + 64u * t;
-            const uint32_t bb = b_base + 2u * kb * kBImageBytes;
-            const uint32_t alo = a + tiles * kTileBytes;
-            mma_f16(dm, make_smem_desc(a, 4096, 1024, 2), make_smem_desc(bb, 128, 512, 0), idesc64, 0);
-            mma_f16(dm + 32u, make_smem_desc(alo, 4096, 1024, 2), make_smem_desc(bb, 128, 512, 0), idesc, 1);
-            mma_f16(dm, make_smem_desc(a + 2048, 4096, 1024, 2), make_smem_desc(bb + 256, 128, 512, 0),
-                    idesc64, 1);
-            mma_f16(dm + 32u, make_smem_desc(alo + 2048, 4096, 1024, 2),
-                    make_smem_desc(bb + 256, 128, 512, 0), idesc, 1);
+        for (int i = 0; i < 8; ++i) {
+          cmul2(X[i], Y[i], c2, d2, make_float2(-d2.x, -d2.y));
+          if (i < 7) {
+            float2 cn = c2, dn = d2;
+            cmul2(cn, dn, sc, sd, snd);
+            c2 = cn;
+            d2 = dn;
           }
         }
-        mma_commit(mbar_s);
       }
-      // the issuing thread polls the MMA barrier; the others sleep in the
-      // CTA barrier, ordered after the MMAs by the tcgen05 fence pair
-      bool got = true;
-      if (tid == 0) got = mbar_wait_bounded(mbar_s, phase, kWaitLimitCycles);
-      phase ^= 1u;
-      tc_fence_before_sync();
-      if (__syncthreads_or(!got)) {
-        if (tid == 0) atomicExch(p.status, kDevErrTimeout);
-        ok = false;
-        break;
+      if (p.conj_out) {
+        // inverse transform: conj() of the result
+#pragma unroll
+        for (int i = 0; i < 8; ++i) Y[i] = make_float2(-Y[i].x, -Y[i].y);
       }
-      tc_fence_after_sync();
-
-      const bool last = (j == K::S);
-      for (int t = half; t < tiles; t += halves) {
-        const uint32_t row = rp((uint32_t)t * 128u + 32u * quarter + lane);  // logical row of this lane
-        // X[i] = (Re out 2i, Re out 2i+1), Y[i] = (Im out 2i, Im out 2i+1)
-        float2 X[8], Y[8];
-        {
-          const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (SPLIT ? 64u : 32u) * t;
-          float v[32];
-          tmem_ld32_wait(taddr, v);
+      if constexpr (K::DIRECT_OUT) {
+        // lanes hold consecutive output indices: store straight to global
+        if ((int)c < nvalid) {
+          uint32_t* o = (p.out_scatter ? p.out + ow * side_base(p.out_l, t0 + c, p.log2I1, p.log2I2)
+                                       : gout + ow * (c << K::LOG2N)) + ow * kbase;
+          if (K::SPLIT && p.out_f32) {
+            // interleaved FP32 complex straight from the accumulator
+            float2* of = reinterpret_cast<float2*>(o);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              of[(2 * i) * kstep] = make_float2(X[i].x, Y[i].x);
+              of[(2 * i + 1) * kstep] = make_float2(X[i].y, Y[i].y);
+            }
+            return;
+          }
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            X[i] = make_float2(v[2 * i], v[2 * i + 1]);
-            Y[i] = make_float2(v[16 + 2 * i], v[16 + 2 * i + 1]);
-          }
-          if constexpr (SPLIT) {
-            tmem_ld32_wait(taddr + 32u, v);
-            const float2 s = make_float2(1.0f / 2048.0f, 1.0f / 2048.0f);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              X[i] = __ffma2_rn(make_float2(v[2 * i], v[2 * i + 1]), s, X[i]);
-              Y[i] = __ffma2_rn(make_float2(v[16 + 2 * i], v[16 + 2 * i + 1]), s, Y[i]);
-            }
-          }
-        }
-        if (row >= rows_valid) continue;  // padding rows of a partial last tile
-
-        // butterfly identity of this row at stage j: sub-transform g, the
-        // digits kk = (k_1 .. k_{j-1}) already produced, and nrest = n^(j+1)
-        uint32_t g, nrest, kk;
-        uint32_t k0row = 0;  // k0 of the row (stage 1)
-        if (j == 1) {
-          kk = 0;
-          const uint32_t lk = (uint32_t)log2C + K::LOG2LQ;  // rows per k0
-          k0row = row >> lk;
-          const uint32_t rem = row & ((1u << lk) - 1u);
-          uint32_t c1;
-          if constexpr (K::IN_C) {
-            c1 = rem >> K::LOG2LQ;
-            nrest = rem & (K::LQ - 1);
-          } else {
-            nrest = rem >> log2C;
-            c1 = rem & ((1u << log2C) - 1u);
-          }
-          g = (k0row << log2C) + c1;
-        } else {
-          const int sj = 4 * (j - 1);
-          kk = row & ((1u << sj) - 1u);
-          const uint32_t q = row >> sj;
-          const int sr = 4 * (K::S - j);
-          g = q >> sr;
-          nrest = q & ((1u << sr) - 1u);
-        }
-
-        if (!last) {
-          // twiddle of output k: a b^k with (a, b) from the stage table:
-          // stage 1: a = W_N^{k0 nrest}, b = W_{L}^{nrest}; stage j >= 2:
-          // a = 1, b = W_{L_j}^{nrest}.  Pairs (a b^{2i}, a b^{2i+1}) are
-          // advanced by b^2 in packed FP32x2 arithmetic.
-          {
-            int toff = 0;
-            if (j >= 2) toff = K::RX << K::LOG2LQ;
-#pragma unroll
-            for (int i = 2; i < j; ++i) toff += 1 << (4 * (K::S - i));
-            const int ent = toff + (j == 1 ? (int)((k0row << K::LOG2LQ) + nrest) : (int)nrest);
-            const float4 e = __ldg(p.stw + ent);
-            const float2 a = make_float2(e.x, e.y), b = make_float2(e.z, e.w);
-            const float2 ab = cmulf(a, b), b2 = cmulf(b, b);
-            float2 c2 = make_float2(a.x, ab.x), d2 = make_float2(a.y, ab.y);
-            const float2 sc = make_float2(b2.x, b2.x), sd = make_float2(b2.y, b2.y);
-            const float2 snd = make_float2(-b2.y, -b2.y);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              cmul2(X[i], Y[i], c2, d2, make_float2(-d2.x, -d2.y));
-              if (i < 7) {
-                float2 cn = c2, dn = d2;
-                cmul2(cn, dn, sc, sd, snd);
-                c2 = cn;
-                d2 = dn;
-              }
-            }
-          }
-          const int sh = 4 * (K::S - j - 1);
-          const uint32_t nnext = nrest >> sh;
-          const uint32_t nlow = nrest & ((1u << sh) - 1u);
-          const uint32_t dr = ((((g << sh) + nlow) << (4 * j)) + (kk << 4));
-          const RowChunks rc = row_chunks(dr, nnext);
-          uint32_t hr[8], hi[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            hr[i] = f2h2(X[i].x, X[i].y);
-            hi[i] = f2h2(Y[i].x, Y[i].y);
-          }
-          *reinterpret_cast<uint4*>(A + rc.re0) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
-          *reinterpret_cast<uint4*>(A + rc.re0 + 2048) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-          *reinterpret_cast<uint4*>(A + rc.re1) = make_uint4(hr[4], hr[5], hr[6], hr[7]);
-          *reinterpret_cast<uint4*>(A + rc.re1 + 2048) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
-          if constexpr (SPLIT) {
-            uint32_t lr[8], li[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              lr[i] = split_lo(X[i].x, X[i].y, hr[i]);
-              li[i] = split_lo(Y[i].x, Y[i].y, hi[i]);
-            }
-            uint8_t* Alo = A + tiles * kTileBytes;
-            *reinterpret_cast<uint4*>(Alo + rc.re0) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
-            *reinterpret_cast<uint4*>(Alo + rc.re0 + 2048) = make_uint4(li[0], li[1], li[2], li[3]);
-            *reinterpret_cast<uint4*>(Alo + rc.re1) = make_uint4(lr[4], lr[5], lr[6], lr[7]);
-            *reinterpret_cast<uint4*>(Alo + rc.re1 + 2048) = make_uint4(li[4], li[5], li[6], li[7]);
-          }
-        } else {
-          // final stage: natural-order outputs into the staging copy
-          uint32_t rev = 0;
-          {
-            uint32_t x = kk;
-#pragma unroll
-            for (int d = 0; d < K::S - 1; ++d) {
-              rev = (rev << 4) | (x & 15u);
-              x >>= 4;
-            }
-          }
-          const uint32_t k0 = g >> log2C;
-          const uint32_t c = g & ((1u << log2C) - 1u);
-          const uint32_t kbase = k0 + (rev << K::LOG2RX);           // output index at k_S = 0
-          constexpr uint32_t kstep = (uint32_t)K::LQ << K::LOG2RX;  // output index step per k_S
-          if (p.otw_level) {
-            // W_M^{col (kbase + kstep k)}: powers of ws = W_M^{col kstep} from
-            // w0 = W_M^{col kbase}, advanced two outputs at a time
-            const int64_t t = t0 + c;
-            const uint32_t col = (p.otw_level == 1)
-                                     ? (uint32_t)(t & ((int64_t(1) << p.log2I1) - 1))
-                                     : (uint32_t)((t >> p.log2I1) & ((int64_t(1) << p.log2I2) - 1));
-            const float2 w0 = tw_lookup(p.otw_lo, p.otw_hi, col * kbase, p.otw_log2M, p.otw_log2S);
-            const float2 ws = tw_lookup(p.otw_lo, p.otw_hi, col * kstep, p.otw_log2M, p.otw_log2S);
-            const float2 w1 = cmulf(w0, ws), ws2 = cmulf(ws, ws);
-            float2 c2 = make_float2(w0.x, w1.x), d2 = make_float2(w0.y, w1.y);
-            const float2 sc = make_float2(ws2.x, ws2.x), sd = make_float2(ws2.y, ws2.y);
-            const float2 snd = make_float2(-ws2.y, -ws2.y);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              cmul2(X[i], Y[i], c2, d2, make_float2(-d2.x, -d2.y));
-              if (i < 7) {
-                float2 cn = c2, dn = d2;
-                cmul2(cn, dn, sc, sd, snd);
-                c2 = cn;
-                d2 = dn;
-              }
-            }
-          }
-          if (p.conj_out) {
-            // inverse transform: conj() of the result
-#pragma unroll
-            for (int i = 0; i < 8; ++i) Y[i] = make_float2(-Y[i].x, -Y[i].y);
-          }
-          if constexpr (K::DIRECT_OUT) {
-            // lanes hold consecutive output indices: store straight to global
-            if ((int)c < nvalid) {
-              uint32_t* o = (p.out_scatter ? p.out + ow * side_base(p.out_l, t0 + c, p.log2I1, p.log2I2)
-                                           : gout + ow * (c << LOG2N)) + ow * kbase;
-              if (SPLIT && p.out_f32) {
-                // interleaved FP32 complex straight from the accumulator
-                float2* of = reinterpret_cast<float2*>(o);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                  of[(2 * i) * kstep] = make_float2(X[i].x, Y[i].x);
-                  of[(2 * i + 1) * kstep] = make_float2(X[i].y, Y[i].y);
-                }
-                continue;
-              }
-#pragma unroll
-              for (int i = 0; i < 8; ++i) {
-                const uint32_t h0 = f2h2(X[i].x, Y[i].x), h1 = f2h2(X[i].y, Y[i].y);
-                o[(2 * i) * kstep] = h0;
-                o[(2 * i + 1) * kstep] = h1;
-                if constexpr (SPLIT) {
-                  o[p.out_plane + (2 * i) * kstep] = split_lo(X[i].x, Y[i].x, h0);
-                  o[p.out_plane + (2 * i + 1) * kstep] = split_lo(X[i].y, Y[i].y, h1);
-                }
-              }
-            }
-            continue;
-          }
-          uint32_t* stg = reinterpret_cast<uint32_t*>(A);
-          const uint32_t base = K::OUT_C ? ((c << LOG2N) + kbase) : ((kbase << log2C) + c);
-          // bank-spreading key; for tensor-map stores the map's swizzle (the
-          // 16-byte chunk index XOR the 128-byte line index, over rows of
-          // C * 4 bytes), which is constant over a thread's 16 words here
-          uint32_t key = stg_key<K>(c, kbase, log2C) << 2;
-          if constexpr (K::OUT_C) {
-            if (K::S == 3 && p.out_tma) key = ((base >> 5) & 7u) << 2;  // rows of 32 points
-          } else {
-            if (p.out_tma) key = ((base >> 5) & ((1u << (log2C - 2)) - 1u)) << 2;
-          }
-          const uint32_t wstep = K::OUT_C ? kstep : (kstep << log2C);
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const uint32_t i0 = (base + (2 * i) * wstep) ^ key;
-            const uint32_t i1 = (base + (2 * i + 1) * wstep) ^ key;
-            if (SPLIT && p.out_f32) {
-              // FP32 output: the two staging planes hold re and im
-              stg[i0] = __float_as_uint(X[i].x);
-              stg[i1] = __float_as_uint(X[i].y);
-              stg[P + i0] = __float_as_uint(Y[i].x);
-              stg[P + i1] = __float_as_uint(Y[i].y);
-              continue;
-            }
             const uint32_t h0 = f2h2(X[i].x, Y[i].x), h1 = f2h2(X[i].y, Y[i].y);
-            stg[i0] = h0;
-            stg[i1] = h1;
-            if constexpr (SPLIT) {
-              stg[P + i0] = split_lo(X[i].x, Y[i].x, h0);
-              stg[P + i1] = split_lo(X[i].y, Y[i].y, h1);
+            o[(2 * i) * kstep] = h0;
+            o[(2 * i + 1) * kstep] = h1;
+            if constexpr (K::SPLIT) {
+              o[p.out_plane + (2 * i) * kstep] = split_lo(X[i].x, Y[i].x, h0);
+              o[p.out_plane + (2 * i + 1) * kstep] = split_lo(X[i].y, Y[i].y, h1);
             }
           }
         }
+        return;
       }
-      fence_proxy_async_smem();
-      tc_fence_before_sync();
-      __syncthreads();
-    }
+      staging_store<K>(p, A, (uint32_t)1 << (log2C + K::LOG2N), log2C, c, kbase, X, Y);
+    };
+    ok = run_stages<K>(p, cx, tiles, log2C, fin);
     if (!ok) break;
 
-    // copy-out: staging (natural order, chunk-swizzled) -> global, 16-byte stores
-    if constexpr (!K::DIRECT_OUT) {
-      const uint4* stg = reinterpret_cast<const uint4*>(A);
-      const uint32_t nch = P >> 2;
-      if (K::OUT_C && K::S == 3 && p.out_tma) {
-        // rows of 32 points in the 128-byte swizzle, up to 256 rows per box;
-        // rows past the end of the output are not written
-        if (tid == 0) {
-          const int row0 = (int)((gout - p.out) >> 5);
-          const uint32_t a0 = smem_u32(A);
-          for (int pl = 0; pl < K::PLANES; ++pl)
-            for (uint32_t r0 = 0; r0 < (P >> 5); r0 += 256)
-              tma_store_5d(&p.out_map, a0 + (uint32_t)pl * (P * 4u) + r0 * 128u, 0, row0 + (int)r0, pl, 0, 0);
-          bulk_commit();
-          bulk_wait_read();  // the staging copy (= A) is rewritten by the next chunk
-        }
-      } else if constexpr (K::OUT_C) {
-        const uint32_t vchunks = ((uint32_t)nvalid << LOG2N) >> 2;
-        for (uint32_t q = tid; q < vchunks; q += blockDim.x) {
-          const uint32_t c = (q << 2) >> LOG2N;
-          const uint32_t ko = (q << 2) & (K::N - 1);
-          const uint32_t pq = q ^ stg_key<K>(c, ko, log2C);
-          uint32_t* o = p.out_scatter ? p.out + ow * (side_base(p.out_l, t0 + c, p.log2I1, p.log2I2) + ko)
-                                      : gout + ow * (q << 2);
-          if (SPLIT && p.out_f32) {
-            // four points: re and im planes -> interleaved FP32 complex
-            const uint4 re = stg[pq], im = stg[nch + pq];
-            reinterpret_cast<uint4*>(o)[0] = make_uint4(re.x, im.x, re.y, im.y);
-            reinterpret_cast<uint4*>(o)[1] = make_uint4(re.z, im.z, re.w, im.w);
-            continue;
-          }
-          *reinterpret_cast<uint4*>(o) = stg[pq];
-          if constexpr (SPLIT) *reinterpret_cast<uint4*>(o + p.out_plane) = stg[nch + pq];
-        }
-      } else if (p.out_tma) {
-        // tensor-map boxes of C columns x 256 elements per plane, one thread
-        if (tid == 0) {
-          const int64_t t1 = t0 & ((int64_t(1) << p.log2I1) - 1);
-          const int64_t t23 = t0 >> p.log2I1;
-          const int t2 = (int)(t23 & ((int64_t(1) << p.log2I2) - 1));
-          const int t3 = (int)(t23 >> p.log2I2);
-          const uint32_t a0 = smem_u32(A);
-          for (int pl = 0; pl < K::PLANES; ++pl)
-            for (int e0 = 0; e0 < K::N; e0 += 256)
-              tma_store_5d(&p.out_map, a0 + (uint32_t)pl * (P * 4u) + ((uint32_t)e0 << log2C) * 4u, (int)t1, e0,
-                           t2, t3, pl);
-          bulk_commit();
-          bulk_wait_read();  // the staging copy (= A) is rewritten by the next chunk
-        }
-      } else {
-        const int cq = log2C - 2;  // log2 of the chunks per output element index
-        const uint32_t es = p.out_l.es;
-        for (uint32_t q = tid; q < nch; q += blockDim.x) {
-          const uint32_t ko = q >> cq;
-          const uint32_t cc = (q & ((1u << cq) - 1u)) << 2;
-          const uint32_t off = ko * es + cc;
-          const uint32_t pq = q ^ stg_key<K>(cc, ko, log2C);
-          if (SPLIT && p.out_f32) {
-            const uint4 re = stg[pq], im = stg[nch + pq];
-            uint4* o = reinterpret_cast<uint4*>(gout + 2u * off);
-            o[0] = make_uint4(re.x, im.x, re.y, im.y);
-            o[1] = make_uint4(re.z, im.z, re.w, im.w);
-            continue;
-          }
-          *reinterpret_cast<uint4*>(gout + off) = stg[pq];
-          if constexpr (SPLIT) *reinterpret_cast<uint4*>(gout + p.out_plane + off) = stg[nch + pq];
-        }
-      }
-    }
+    // copy-out: staging (natural order, chunk-swizzled) -> global
+    if constexpr (!K::DIRECT_OUT) copy_out<K>(p, A, gout, t0, nvalid, log2C);
     __syncthreads();  // staging (= A) is rewritten by the next chunk
   }
 

@@ -93,6 +93,19 @@ struct PassParams {
   int* status;            // device error word (0 = ok)
 };
 
+// A fused 2D pass: S x S matrices, one per cluster of 2^log2K CTAs.  CTA r
+// of a cluster transforms rows r*S/K .. (r+1)*S/K - 1 of its matrix (phase 1,
+// `row`: contiguous rows read from row.in), hands every row output to the CTA
+// that owns its column through distributed shared memory, then transforms
+// columns r*S/K .. (r+1)*S/K - 1 (phase 2, `col`: strided output to col.out).
+// One read and one write of every matrix in HBM.
+struct Fused2DParams {
+  PassParams row;
+  PassParams col;
+  int log2K;      // CTAs per cluster (log2)
+  int64_t batch;  // matrices
+};
+
 constexpr int kTileRows = 128;        // butterflies per MMA tile (M)
 constexpr int kTileBytes = 8192;      // one tile of A: 128 rows x 32 halves
 constexpr int kBImageBytes = 2048;    // 32 x 32 halves, K-major, no swizzle
@@ -101,6 +114,11 @@ constexpr long long kWaitLimitCycles = 2000000000LL;  // ~1 s at 2 GHz
 
 // Device status codes written by kernels (mirror tcfft_status values).
 constexpr int kDevErrTimeout = 5;
+
+// Largest side (log2) of the fused 2D kernels: 2^18 points over at most 16
+// CTAs of 16384 points (plain), 2^16 over 16 CTAs of 4096 (split).
+constexpr int kMaxLog2Fused2D = 9;
+constexpr int kMaxLog2Fused2DSplit = 8;
 
 // Supported pass lengths per mode and precision (log2 N).
 constexpr int kMinLog2Pass = 4;

@@ -383,4 +383,121 @@ tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int
   return TCFFT_OK;
 }
 
+// ------------------------------------------------------------ fused 2D
+tcfft_status fused2d_geometry(Fused2DLaunch& fl, int64_t S, int64_t batch, bool split, int force_log2K) {
+  std::memset(&fl.f, 0, sizeof(fl.f));
+  const int log2S = ilog2(S);
+  fl.fn = fused2d_fn(log2S, split);
+  if (!fl.fn || !is_pow2(S) || batch < 1) return TCFFT_ERR_INVALID_SIZE;
+  const int64_t pts = S * S;
+  const int64_t pmax = split ? 4096 : 8192;
+  int log2K = 0;
+  if (force_log2K >= 0) {
+    log2K = force_log2K;
+  } else {
+    while ((pts >> log2K) > pmax && log2K < 4) ++log2K;
+    if ((pts >> log2K) > pmax && (split || (pts >> log2K) > 2 * pmax)) return TCFFT_ERR_INVALID_SIZE;
+  }
+  const int64_t K = int64_t(1) << log2K, C = S / K, P = pts / K;
+  if (log2K > 4 || C < 8 || P > (split ? pmax : 2 * pmax)) return TCFFT_ERR_INVALID_SIZE;
+  const int planes = split ? 2 : 1;
+  const int S1 = log2S / 4, RX = 1 << (log2S % 4);
+  if (S1 >= 2 && RX > 1 && (C << (4 * (S1 - 1))) < 128) return TCFFT_ERR_INVALID_SIZE;  // one k0 per MMA tile
+  const int tiles = (int)((P + 2047) / 2048);
+  int cols = 32;
+  while (cols < 32 * tiles * planes) cols *= 2;
+  if (cols > 512) return TCFFT_ERR_INVALID_SIZE;
+  for (PassParams* p : {&fl.f.row, &fl.f.col}) {
+    p->log2N = log2S;
+    p->log2C = ilog2(C);
+    p->tiles = tiles;
+    p->tmem_cols = cols;
+    p->T = batch * S;
+    p->prescale = 1.0f;
+    p->nchunks = batch;
+  }
+  // rows: contiguous transforms of length S; columns: element e of column c
+  // at c + e S (matrix m at m S^2), the stage-1 reads from the row phase's
+  // exchange buffer in its 128-byte-line swizzle
+  fl.f.row.log2I1 = 40;
+  fl.f.row.in_l = SideLayout{S, 0, 0, 1, nullptr};
+  fl.f.row.out_l = fl.f.row.in_l;
+  fl.f.row.async_load = 1;
+  fl.f.col.log2I1 = log2S;
+  fl.f.col.log2I2 = 40;
+  fl.f.col.in_l = SideLayout{1, pts, 0, (uint32_t)S, nullptr};
+  fl.f.col.out_l = fl.f.col.in_l;
+  fl.f.col.in_swz = 3;
+  fl.f.col.out_tma = (log2S >= 8 && C <= 32 && !env_int("TCFFT_NO_TMA", 0)) ? 1 : 0;
+  fl.f.log2K = log2K;
+  fl.f.batch = batch;
+  const int nb = (S1 >= 2 && RX > 1) ? RX : 1;
+  fl.smem = 1008 + (size_t)planes * tiles * kTileBytes + (size_t)planes * P * 4 + (size_t)planes * nb * kBImageBytes;
+  if (fl.smem > 227 * 1024) return TCFFT_ERR_INVALID_SIZE;
+  fl.threads = tiles >= 2 ? 256 : 128;
+  if (cudaFuncSetAttribute(fl.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
+    return TCFFT_ERR_CUDA;
+  if (cudaFuncSetAttribute(fl.fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
+    return TCFFT_ERR_CUDA;
+  if (K > 8 && cudaFuncSetAttribute(fl.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return TCFFT_ERR_UNSUPPORTED;
+  }
+  // clusters that can be resident at once: the persistent grid
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(K * std::min<int64_t>(batch, 65536)));
+  cfg.blockDim = dim3((unsigned)fl.threads);
+  cfg.dynamicSmemBytes = fl.smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)K;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, fl.fn, &cfg) != cudaSuccess || nclusters < 1) {
+    (void)cudaGetLastError();
+    return TCFFT_ERR_INVALID_SIZE;  // the cluster cannot be placed at all
+  }
+  // CTAs per SM from registers, shared memory, threads and TMEM columns (as
+  // for the pass kernels); clusters never wait on one another, so a grid
+  // larger than what is resident at once only queues clusters
+  int dev = 0, sms = 1, smem_sm = 0, regs_sm = 0, thr_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, fl.fn) != cudaSuccess) return TCFFT_ERR_CUDA;
+  fl.regs = fa.numRegs;
+  const int warp_regs = ((fa.numRegs * 32 + 255) / 256) * 256;
+  const int occ = std::min(std::min(512 / cols, regs_sm / (warp_regs * (fl.threads / 32))),
+                           std::min(smem_sm / (int)(fl.smem + fa.sharedSizeBytes + 1024), thr_sm / fl.threads));
+  fl.occ = std::max(1, occ);
+  const int64_t est = std::max<int64_t>(nclusters, (int64_t)fl.occ * sms / K);
+  fl.grid = dim3((unsigned)(K * std::min<int64_t>(batch, est)));
+  return TCFFT_OK;
+}
+
+cudaError_t launch_fused2d(const Fused2DLaunch& fl, const Fused2DParams& f, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = fl.grid;
+  cfg.blockDim = dim3((unsigned)fl.threads);
+  cfg.dynamicSmemBytes = fl.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1u << f.log2K;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  void* args[1] = {const_cast<Fused2DParams*>(&f)};
+  return cudaLaunchKernelExC(&cfg, fl.fn, args);
+}
+
 }  // namespace tcfft

@@ -61,4 +61,32 @@ tcfft_status pass_geometry(PassLaunch& ps, int64_t L, int64_t T, int64_t I1, int
                            Side out, bool split, int64_t target_points = 0, int force_threads = 0,
                            int force_async = -1, bool share_sm = false);
 
+// ------------------------------------------------------------ fused 2D
+// One fused 2D pass (Fused2DParams): S x S matrices, a cluster of 2^log2K
+// CTAs per matrix.
+struct Fused2DLaunch {
+  Fused2DParams f;
+  const void* fn = nullptr;
+  dim3 grid;
+  int threads = kThreads;
+  size_t smem = 0;
+  int occ = 0;  // CTAs per SM
+  int regs = 0;
+};
+
+// Kernel entry point of the fused 2D pass for S = 2^log2S, or null.
+const void* fused2d_fn(int log2S, bool split);
+
+// Fills the geometry of a fused 2D pass over `batch` S x S matrices: the
+// smallest cluster (2^log2K CTAs, at most 16) whose CTAs hold at most 8192
+// points each (4096 split; 16384 plain when 16 CTAs of 8192 do not suffice)
+// and at least 8 columns each; tables, buffers and direction flags are left
+// to the caller.  TCFFT_ERR_INVALID_SIZE when the matrix does not fit (or
+// force_log2K >= 0 names an impossible cluster).
+tcfft_status fused2d_geometry(Fused2DLaunch& fl, int64_t S, int64_t batch, bool split, int force_log2K = -1);
+
+// Launches a fused 2D pass (cluster dimension and programmatic stream
+// serialization attributes) on `s`.
+cudaError_t launch_fused2d(const Fused2DLaunch& fl, const Fused2DParams& f, cudaStream_t s);
+
 }  // namespace tcfft

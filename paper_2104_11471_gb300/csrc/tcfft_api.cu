@@ -62,6 +62,11 @@ struct Pass : PassLaunch {
   Buf src, dst;
   int64_t src_off = 0, dst_off = 0;  // element offsets into the workspace
   int group = 0;                     // independent branch of a ragged plan
+  // fused 2D pass (one launch for rows and columns): p is the row phase, p2
+  // the column phase, 2^log2K CTAs per cluster (one matrix per cluster)
+  int fused = 0;
+  PassParams p2;
+  int log2K = 0;
 };
 
 struct GraphEntry {
@@ -86,6 +91,7 @@ struct tcfft_plan_s {
   bool split = false;
   bool fp32 = false;      // TCFFT_FP32: user buffers are interleaved FP32 complex (split kernels inside)
   bool share_sm = false;  // TCFFT_PLAN_SHARE_SM
+  bool fused_2d = false;  // TCFFT_PLAN_FUSED_2D
   int64_t points = 0;  // total complex points per plane
   std::vector<Pass> passes;
   std::map<int, TwTable> tables;
@@ -218,6 +224,8 @@ tcfft_status tune_pass(tcfft_plan_s* pl, Pass& ps, int64_t L, int64_t T, int64_t
                        Side out, int otw_level, int log2M);
 
 PassParams bound_params(const tcfft_plan_s* plan, const Pass& ps, const void* in, void* out);
+cudaError_t launch_plan_pass(const tcfft_plan_s* plan, const Pass& ps, const void* in, void* out, cudaStream_t s,
+                             int64_t batch = 0);
 
 tcfft_status add_pass(tcfft_plan_s* pl, int64_t L, int64_t T, int64_t I1, int64_t I2, Side in,
                       Side out, Buf src, Buf dst, int otw_level, int log2M, int group = 0,
@@ -235,6 +243,50 @@ tcfft_status add_pass(tcfft_plan_s* pl, int64_t L, int64_t T, int64_t I1, int64_
   if (pl->autotune) {
     st = tune_pass(pl, ps, L, T, I1, I2, in, out, otw_level, log2M);
     if (st != TCFFT_OK) return st;
+  }
+  pl->passes.push_back(ps);
+  return TCFFT_OK;
+}
+
+// Adds one fused 2D pass over B matrices of S x S (rows and columns in one
+// launch, Sec. 3.1), reading `src` and writing `dst`; toff: optional table of
+// the matrices' first elements (ragged batches).
+tcfft_status add_fused_pass(tcfft_plan_s* pl, int64_t S, int64_t B, Buf src, Buf dst, int group = 0,
+                            const int64_t* toff = nullptr) {
+  Fused2DLaunch fl;
+  tcfft_status st = fused2d_geometry(fl, S, B, pl->split);
+  if (st != TCFFT_OK) return st;
+  if (pl->share_sm) fl.grid.x = std::max(1u << fl.f.log2K, (fl.grid.x / 2) & ~((1u << fl.f.log2K) - 1u));
+  Pass ps;
+  ps.fused = 1;
+  ps.fn = fl.fn;
+  ps.grid = fl.grid;
+  ps.threads = fl.threads;
+  ps.smem = fl.smem;
+  ps.occ = fl.occ;
+  ps.regs = fl.regs;
+  ps.p = fl.f.row;
+  ps.p2 = fl.f.col;
+  ps.log2K = fl.f.log2K;
+  ps.src = src;
+  ps.dst = dst;
+  ps.group = group;
+  st = bind_tables(pl, ps, ilog2(S), 0, 0);
+  if (st != TCFFT_OK) return st;
+  // both phases have length S: the same tables and DFT images
+  PassParams& c = ps.p2;
+  c.tw_lo = ps.p.tw_lo;
+  c.tw_hi = ps.p.tw_hi;
+  c.tw_log2S = ps.p.tw_log2S;
+  c.stw = ps.p.stw;
+  c.dft_b = ps.p.dft_b;
+  c.status = ps.p.status;
+  c.in_plane = ps.p.in_plane;
+  c.out_plane = ps.p.out_plane;
+  if (toff) {
+    ps.p.in_l.toff = toff;
+    c.out_l.toff = toff;
+    c.out_tma = 0;
   }
   pl->passes.push_back(ps);
   return TCFFT_OK;
@@ -502,11 +554,8 @@ float time_passes(tcfft_plan_s* pl) {
   bool ok = true;
   for (int rep = 0; rep < 4 && ok; ++rep) {
     cudaEventRecord(e0);
-    for (const Pass& ps : pl->passes) {
-      PassParams p = bound_params(pl, ps, pl->tune_buf, pl->tune_buf);
-      void* args[1] = {&p};
-      if (launch_pass(ps.fn, ps.grid, ps.threads, ps.smem, 0, args) != cudaSuccess) ok = false;
-    }
+    for (const Pass& ps : pl->passes)
+      if (launch_plan_pass(pl, ps, pl->tune_buf, pl->tune_buf, 0) != cudaSuccess) ok = false;
     cudaEventRecord(e1);
     cudaEventSynchronize(e1);
     float t = 0.0f;
@@ -638,9 +687,49 @@ tcfft_status build_2d(tcfft_plan_s* pl, int col_l1) {
   return add_pass(pl, N2, B * ny * N1, ny, N1, bi, bo, BUF_WS, BUF_OUT, 0, 0);
 }
 
+bool fused_2d_available(const tcfft_plan_s* pl, int64_t nx, int64_t ny, int64_t B) {
+  if (!pl->fused_2d || nx != ny || env_int("TCFFT_NO_FUSED_2D", 0)) return false;  // tuning override
+  Fused2DLaunch fl;
+  return fused2d_geometry(fl, nx, B, pl->split) == TCFFT_OK;
+}
+
 tcfft_status plan_2d(tcfft_plan_s* pl) {
   const int64_t nx = pl->nx, B = pl->batch;
   const int64_t mat = nx * pl->ny;
+  // TCFFT_PLAN_FUSED_2D, square matrices up to 512^2 (256^2 split): rows and
+  // columns in one fused launch, one HBM read and one write per matrix
+  // (Sec. 3.1); with autotuning the fused launch competes with the two-pass
+  // plan.  Measured at 2^28 points: 256^2 fused 1.71 ms, two passes 0.79 ms;
+  // 64^2 1.66 vs 1.34 ms (the stages are bound by on-chip work, not HBM)
+  if (fused_2d_available(pl, nx, pl->ny, B)) {
+    bool fused = true;
+    if (pl->autotune) {
+      char key[128];
+      std::snprintf(key, sizeof(key), "fused_v1_s%d_p%d_T%d_h%d", ilog2(nx), pl->split ? 1 : 0, ilog2(B),
+                    pl->share_sm ? 1 : 0);
+      int64_t code = -1;
+      {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        tune_load();
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) code = it->second;
+      }
+      if (code < 0) {
+        float tf = -1.0f, tu = -1.0f;
+        if (add_fused_pass(pl, nx, B, BUF_IN, BUF_OUT) == TCFFT_OK) tf = time_passes(pl);
+        pl->passes.clear();
+        const int64_t cap = pl->split ? kCapSplit : kCapPlain;
+        if (8 * nx <= cap && ilog2(nx) <= max_strided_log2(pl) && build_2d(pl, 0) == TCFFT_OK) tu = time_passes(pl);
+        pl->passes.clear();
+        code = (tf > 0.0f && (tu <= 0.0f || tf <= tu)) ? 1 : 0;
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = code;
+        tune_store();
+      }
+      fused = code == 1;
+    }
+    if (fused) return add_fused_pass(pl, nx, B, BUF_IN, BUF_OUT);
+  }
   const int64_t cap = pl->split ? kCapSplit : kCapPlain;
   const int lg = ilog2(nx);
   const size_t ws = (size_t)B * mat * 4 * (pl->split ? 2 : 1);
@@ -753,6 +842,9 @@ tcfft_status plan_many(tcfft_plan_s* pl, int64_t count, const int64_t* n0, const
         st = add_pass(pl, N2, k * N1, N1, kNoLevel, in2, out2, BUF_WS, BUF_OUT, 0, 0, gid, ws_off, 0);
         ws_off += k * n;
       }
+    } else if (fused_2d_available(pl, a, b, k)) {
+      // square matrices: rows and columns in one fused launch
+      st = add_fused_pass(pl, a, k, BUF_IN, BUF_OUT, gid, toff);
     } else {
       const int64_t nx = a, ny = b;
       if (8 * nx > cap) return TCFFT_ERR_INVALID_SIZE;  // ragged 2D keeps columns in one pass
@@ -768,8 +860,8 @@ tcfft_status plan_many(tcfft_plan_s* pl, int64_t count, const int64_t* n0, const
   return TCFFT_OK;
 }
 
-constexpr unsigned kPlanFlags =
-    TCFFT_PLAN_AUTOTUNE | TCFFT_PLAN_GRAPH | TCFFT_PLAN_INVERSE | TCFFT_PLAN_SCALE | TCFFT_PLAN_SHARE_SM;
+constexpr unsigned kPlanFlags = TCFFT_PLAN_AUTOTUNE | TCFFT_PLAN_GRAPH | TCFFT_PLAN_INVERSE | TCFFT_PLAN_SCALE |
+                                TCFFT_PLAN_SHARE_SM | TCFFT_PLAN_FUSED_2D;
 
 void apply_flags(tcfft_plan_s* pl, unsigned flags) {
   pl->autotune = (flags & TCFFT_PLAN_AUTOTUNE) || env_int("TCFFT_AUTOTUNE", 0);
@@ -777,6 +869,7 @@ void apply_flags(tcfft_plan_s* pl, unsigned flags) {
   pl->inverse = (flags & TCFFT_PLAN_INVERSE) != 0;
   pl->normalise = (flags & TCFFT_PLAN_SCALE) != 0;
   pl->share_sm = (flags & TCFFT_PLAN_SHARE_SM) != 0;
+  pl->fused_2d = (flags & TCFFT_PLAN_FUSED_2D) != 0;
 }
 
 // Direction and scaling: the inverse DFT is conj(DFT(conj(x))), so the first
@@ -790,12 +883,15 @@ void apply_direction(tcfft_plan_s* pl) {
     size_t j = i;
     while (j + 1 < pl->passes.size() && pl->passes[j + 1].group == pl->passes[i].group) ++j;
     pl->passes[i].p.conj_in = pl->inverse ? 1 : 0;
-    pl->passes[j].p.conj_out = pl->inverse ? 1 : 0;
+    (pl->passes[j].fused ? pl->passes[j].p2 : pl->passes[j].p).conj_out = pl->inverse ? 1 : 0;
     // 1/N is spread over the transform: every radix-16 stage uses F_16 / 16
     // (scaled DFT-matrix images, bound in bind_tables) and every leading
     // radix-R step scales by 1/R, so intermediates keep the input's magnitude
     if (pl->normalise)
-      for (size_t k = i; k <= j; ++k) pl->passes[k].p.prescale = 1.0f / (float)(1 << (pl->passes[k].p.log2N % 4));
+      for (size_t k = i; k <= j; ++k) {
+        pl->passes[k].p.prescale = 1.0f / (float)(1 << (pl->passes[k].p.log2N % 4));
+        pl->passes[k].p2.prescale = pl->passes[k].p.prescale;
+      }
     i = j + 1;
   }
 }
@@ -806,7 +902,7 @@ void apply_direction(tcfft_plan_s* pl) {
 void apply_io(tcfft_plan_s* pl) {
   for (Pass& ps : pl->passes) {
     ps.p.in_f32 = (pl->fp32 && ps.src != BUF_WS) ? 1 : 0;
-    ps.p.out_f32 = (pl->fp32 && ps.dst != BUF_WS) ? 1 : 0;
+    (ps.fused ? ps.p2 : ps.p).out_f32 = (pl->fp32 && ps.dst != BUF_WS) ? 1 : 0;
   }
 }
 
@@ -866,6 +962,69 @@ PassParams bound_params(const tcfft_plan_s* plan, const Pass& ps, const void* in
   return p;
 }
 
+// A fused pass's parameters with the exec's buffers: the rows read `in`'s
+// side of the pass, the columns write its output side; batch > 0 runs the
+// first `batch` matrices of a dense plan (user buffers of `batch` matrices).
+Fused2DParams bound_fused(const tcfft_plan_s* plan, const Pass& ps, const void* in, void* out, int64_t batch = 0) {
+  Fused2DParams f;
+  f.row = ps.p;
+  f.col = ps.p2;
+  f.log2K = ps.log2K;
+  f.batch = ps.p.nchunks;
+  uint32_t* bufs[3] = {reinterpret_cast<uint32_t*>(const_cast<void*>(in)),
+                       reinterpret_cast<uint32_t*>(out), reinterpret_cast<uint32_t*>(plan->ws)};
+  f.row.in = bufs[ps.src] + (ps.src == BUF_WS ? ps.src_off : 0);
+  f.col.out = bufs[ps.dst] + (ps.dst == BUF_WS ? ps.dst_off : 0);
+  f.row.out = f.col.out;
+  f.col.in = f.row.in;
+  if (batch > 0) {
+    const int64_t S = int64_t(1) << ps.p.log2N;
+    f.batch = batch;
+    f.row.T = f.col.T = batch * S;
+    f.row.nchunks = f.col.nchunks = batch;
+    if (ps.src != BUF_WS) f.row.in_plane = batch * S * S;
+    if (ps.dst != BUF_WS) f.col.out_plane = batch * S * S;
+  }
+  encode_out_map(f.col, plan->split);
+  return f;
+}
+
+// Launches pass ps of the plan on `s` with the exec's buffers (the first
+// `batch` transforms of a dense plan when batch > 0).
+cudaError_t launch_plan_pass(const tcfft_plan_s* plan, const Pass& ps, const void* in, void* out, cudaStream_t s,
+                             int64_t batch) {
+  if (ps.fused) {
+    Fused2DLaunch fl;
+    fl.fn = ps.fn;
+    fl.grid = ps.grid;
+    fl.threads = ps.threads;
+    fl.smem = ps.smem;
+    const Fused2DParams f = bound_fused(plan, ps, in, out, batch);
+    const unsigned K = 1u << ps.log2K;
+    if (batch > 0) fl.grid.x = (unsigned)std::min<int64_t>(ps.grid.x, K * batch);
+    return launch_fused2d(fl, f, s);
+  }
+  PassParams p = bound_params(plan, ps, in, out);
+  dim3 grid = ps.grid;
+  if (batch > 0) {
+    const int64_t per = plan->points / plan->batch;  // points of one transform
+    // every pass's transforms are the batch's transforms times a fixed count
+    p.T = ps.p.T / plan->batch * batch;
+    const int64_t C = int64_t(1) << p.log2C;
+    p.nchunks = (p.T + C - 1) / C;
+    // user buffers hold `batch` transforms per plane; the workspace keeps its layout
+    if (ps.src != BUF_WS) p.in_plane = per * batch;
+    if (ps.dst != BUF_WS) p.out_plane = per * batch;
+    grid = dim3((unsigned)std::min<int64_t>(p.nchunks, (int64_t)ps.grid.x));
+    p.in_tma = ps.p.in_tma;  // re-encode for the shorter batch
+    p.out_tma = ps.p.out_tma;
+    encode_in_map(p, plan->split);
+    encode_out_map(p, plan->split);
+  }
+  void* args[1] = {&p};
+  return launch_pass(ps.fn, grid, ps.threads, ps.smem, s, args);
+}
+
 // Replays the plan as one CUDA graph: passes of a group form a chain, the
 // groups of a ragged plan are independent branches that the GPU may run
 // concurrently.  One instantiated graph is kept per (in, out) pair.
@@ -878,8 +1037,10 @@ tcfft_status exec_graph(tcfft_plan_s* plan, const void* in, void* out, cudaStrea
   std::map<int, cudaGraphNode_t> last;  // last node of each group
   tcfft_status st = TCFFT_OK;
   for (const Pass& ps : plan->passes) {
-    PassParams p = bound_params(plan, ps, in, out);
-    void* args[1] = {&p};
+    PassParams p = ps.fused ? ps.p : bound_params(plan, ps, in, out);
+    Fused2DParams f;
+    if (ps.fused) f = bound_fused(plan, ps, in, out);
+    void* args[1] = {ps.fused ? static_cast<void*>(&f) : static_cast<void*>(&p)};
     cudaKernelNodeParams kp = {};
     kp.func = const_cast<void*>(ps.fn);
     kp.gridDim = ps.grid;
@@ -891,6 +1052,16 @@ tcfft_status exec_graph(tcfft_plan_s* plan, const void* in, void* out, cudaStrea
     if (cudaGraphAddKernelNode(&node, graph, nullptr, 0, &kp) != cudaSuccess) {
       st = TCFFT_ERR_CUDA;
       break;
+    }
+    if (ps.fused) {
+      cudaKernelNodeAttrValue v = {};
+      v.clusterDim.x = 1u << ps.log2K;
+      v.clusterDim.y = 1;
+      v.clusterDim.z = 1;
+      if (cudaGraphKernelNodeSetAttribute(node, cudaKernelNodeAttributeClusterDimension, &v) != cudaSuccess) {
+        st = TCFFT_ERR_CUDA;
+        break;
+      }
     }
     if (it != last.end()) {
       // programmatic edge: the pass starts its prologue while the previous
@@ -1052,9 +1223,7 @@ tcfft_status tcfft_exec(tcfft_plan plan, const void* in, void* out, void* stream
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (plan->use_graph) return exec_graph(plan, in, out, s);
   for (const Pass& ps : plan->passes) {
-    PassParams p = bound_params(plan, ps, in, out);
-    void* args[1] = {&p};
-    cudaError_t e = launch_pass(ps.fn, ps.grid, ps.threads, ps.smem, s, args);
+    cudaError_t e = launch_plan_pass(plan, ps, in, out, s);
     if (e != cudaSuccess) {
       if (env_int("TCFFT_DEBUG", 0))
         std::fprintf(stderr, "tcfft_exec: launch of pass (log2n %d, grid %u, smem %zu) failed: %s\n",
@@ -1073,24 +1242,8 @@ tcfft_status tcfft_exec_batch(tcfft_plan plan, const void* in, void* out, int64_
   if ((reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(out) & 15))
     return TCFFT_ERR_INVALID_VALUE;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const int64_t per = plan->points / plan->batch;  // points of one transform
-  for (const Pass& ps : plan->passes) {
-    PassParams p = bound_params(plan, ps, in, out);
-    // every pass's transforms are the batch's transforms times a fixed count
-    p.T = ps.p.T / plan->batch * batch;
-    const int64_t C = int64_t(1) << p.log2C;
-    p.nchunks = (p.T + C - 1) / C;
-    // user buffers hold `batch` transforms per plane; the workspace keeps its layout
-    if (ps.src != BUF_WS) p.in_plane = per * batch;
-    if (ps.dst != BUF_WS) p.out_plane = per * batch;
-    const dim3 grid((unsigned)std::min<int64_t>(p.nchunks, (int64_t)ps.grid.x));
-    p.in_tma = ps.p.in_tma;  // re-encode for the shorter batch
-    p.out_tma = ps.p.out_tma;
-    encode_in_map(p, plan->split);
-    encode_out_map(p, plan->split);
-    void* args[1] = {&p};
-    if (launch_pass(ps.fn, grid, ps.threads, ps.smem, s, args) != cudaSuccess) return TCFFT_ERR_LAUNCH;
-  }
+  for (const Pass& ps : plan->passes)
+    if (launch_plan_pass(plan, ps, in, out, s, batch) != cudaSuccess) return TCFFT_ERR_LAUNCH;
   return TCFFT_OK;
 }
 
@@ -1208,17 +1361,17 @@ size_t tcfft_plan_describe(tcfft_plan plan, char* buf, size_t len) {
   for (size_t i = 0; i < plan->passes.size(); ++i) {
     const Pass& ps = plan->passes[i];
     const PassParams& p = ps.p;
-    const char* modes[3] = {"contig", "strided", "contig_to_strided"};
-    const int mode = (p.in_l.es == 1) ? ((p.out_l.es == 1) ? 0 : 2) : 1;
+    const char* modes[4] = {"contig", "strided", "contig_to_strided", "fused_2d"};
+    const int mode = ps.fused ? 3 : ((p.in_l.es == 1) ? ((p.out_l.es == 1) ? 0 : 2) : 1);
     char tmp[512];
     std::snprintf(tmp, sizeof(tmp),
                   "%s{\"log2n\": %d, \"mode\": \"%s\", \"transforms\": %lld, \"per_cta\": %d, "
                   "\"tiles\": %d, \"tmem_cols\": %d, \"smem\": %zu, \"async_load\": %d, \"grid\": %u, "
                   "\"chunks\": %lld, \"out_twiddle\": %d, \"ctas_per_sm\": %d, \"regs\": %d, "
-                  "\"threads\": %d}",
+                  "\"threads\": %d, \"cluster\": %d}",
                   i ? ", " : "", p.log2N, modes[mode], (long long)p.T, 1 << p.log2C, p.tiles, p.tmem_cols,
                   ps.smem, p.async_load, ps.grid.x, (long long)p.nchunks, p.otw_level, ps.occ, ps.regs,
-                  ps.threads);
+                  ps.threads, 1 << ps.log2K);
     out += tmp;
   }
   out += "]";
