@@ -485,7 +485,9 @@ def build_ragged(args, dev, rank):
     h = _half_draw(2 * pts, 4 + rank)
     x = torch.from_numpy(h.view(np.uint16)).to(dev)
     y = torch.empty_like(x)
-    flags = tc.TCFFT_PLAN_GRAPH | (0 if args.no_autotune else tc.TCFFT_PLAN_AUTOTUNE)
+    tune = 0 if args.no_autotune else tc.TCFFT_PLAN_AUTOTUNE
+    persistent = args.ragged_mode == "persistent"
+    flags = tc.TCFFT_PLAN_PERSISTENT if persistent else (tc.TCFFT_PLAN_GRAPH | tune)
     plan = tc.Plan.plan_many(shapes, tc.TCFFT_FP16, flags)
     flops = sum(5.0 * np.prod(sh) * math.log2(np.prod(sh)) for sh in shapes)
     offs = np.concatenate([[0], np.cumsum([int(np.prod(sh)) for sh in shapes])])
@@ -503,30 +505,38 @@ def build_ragged(args, dev, rank):
             ref = orc.fft_batch(z) if len(shapes[i]) == 1 else orc.fft_2d(z)
             worst = max(worst, orc.rel_l2(g, ref))
         return worst
-    entries = [Entry(f"ragged {len(shapes)} transforms, one graph launch", plan, x, y, flops, 8.0 * pts, check)]
+    how = "one persistent work-queue launch" if persistent else "one graph launch"
+    entries = [Entry(f"ragged {len(shapes)} transforms, {how}", plan, x, y, flops, 8.0 * pts, check)]
     cfg = {"workload": "ragged: 4096 1D transforms N=2^k, k~U{8..16}, + 256 2D transforms side~U{128,256,512,1024}, "
-                       "shuffled into one packed buffer, one tcfft_plan_many plan replayed as one CUDA graph "
-                       "launch per step, geometry from the plan-time autotuner; uniform[-1,1] seeded inputs",
+                       "shuffled into one packed buffer, one tcfft_plan_many plan per step: "
+                       + ("one persistent launch claiming (pass, chunk) items from a device work queue"
+                          if persistent else "replayed as one CUDA graph launch, geometry from the plan-time "
+                          "autotuner") + "; uniform[-1,1] seeded inputs",
            "transforms": len(shapes), "points_per_exec": pts, "precision": "plain FP16",
            "l2": f"inputs {pts * 4 / 2**20:.0f} MiB per exec (> L2), no flush"}
 
     def per_size_launches(steps, stream):
-        """The same plan with one launch per pass (no graph)."""
-        p2 = tc.Plan.plan_many(shapes, tc.TCFFT_FP16, 0 if args.no_autotune else tc.TCFFT_PLAN_AUTOTUNE)
-        for _ in range(2):
-            p2.exec(x, y, stream)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            p2.exec(x, y, stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / steps
-        launches = p2.num_launches
-        p2.destroy()
-        return {"ms_per_step": round(ms, 4), "gflops": round(flops / (ms / 1e3) / 1e9, 1),
-                "launches_per_step": launches}
+        """The same shapes with one launch per pass (no graph), and with the
+        other of the graph / persistent-queue modes."""
+        out = {}
+        modes = [("per_pass", tune), ("graph" if persistent else "persistent",
+                                       (tc.TCFFT_PLAN_GRAPH | tune) if persistent else tc.TCFFT_PLAN_PERSISTENT)]
+        for name, fl in modes:
+            p2 = tc.Plan.plan_many(shapes, tc.TCFFT_FP16, fl)
+            for _ in range(2):
+                p2.exec(x, y, stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                p2.exec(x, y, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            out[name] = {"ms_per_step": round(ms, 4), "gflops": round(flops / (ms / 1e3) / 1e9, 1),
+                         "launches_per_step": p2.num_launches}
+            p2.destroy()
+        return out
     cpu_sizes = [sh for sh in shapes[:64]]
     return entries, cfg, cpu_sizes, (h, None), per_size_launches
 
@@ -867,6 +877,9 @@ def main():
                          "latency: single large transforms")
     ap.add_argument("--precision", default="fp16", choices=["fp16", "split", "fp32"],
                     help="sweep1d: plain FP16 (the benchmark), split FP16, or FP32 in and out")
+    ap.add_argument("--ragged-mode", default="graph", choices=["graph", "persistent"],
+                    help="ragged workload: one CUDA graph launch (default; the persistent work-queue launch is "
+                         "timed beside it) or one persistent work-queue launch")
     ap.add_argument("--no-autotune", action="store_true",
                     help="plan with the fixed geometry heuristics instead of the plan-time autotuner")
     ap.add_argument("--write-traffic", default="", metavar="CSV",

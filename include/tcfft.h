@@ -99,6 +99,15 @@ typedef enum {
                                   and the two-pass plan is faster; with
                                   TCFFT_PLAN_AUTOTUNE the faster of the two is
                                   timed and kept */
+#define TCFFT_PLAN_PERSISTENT 64u /* tcfft_plan_many, plain FP16: every pass of
+                                  every shape group in ONE persistent launch
+                                  that claims (pass, chunk) items from a device
+                                  work queue; a pass starts on a chunk once the
+                                  previous pass of its group has completed (a
+                                  device counter, bounded wait: a wait that
+                                  runs out reports TCFFT_ERR_TIMEOUT through
+                                  tcfft_plan_last_error and skips the rest).
+                                  Other precisions ignore it */
 
 /* Plan a batch of `batch` 1D transforms of length n (the paper's
  * tcfftPlan1D(plan, nx, batch), Sec. 3.1).  Allocates device twiddle tables
@@ -210,6 +219,16 @@ tcfft_status tcfft_exec_1d_noalloc(int64_t n, int64_t batch, const void* in, voi
  * (SM clock cycles, <= 4e9) have passed.  The kernel exits normally; the
  * context stays usable.  Synchronises the device. */
 tcfft_status tcfft_selftest_wait_timeout(long long limit_cycles);
+
+/* Failure-path self-test of the persistent executor (TCFFT_PLAN_PERSISTENT;
+ * no counterpart in the paper): builds a persistent plan of one two-pass
+ * transform of 2^16 points, withholds the first pass's queue items, runs the
+ * launch with dependency waits limited to limit_cycles (SM clock cycles,
+ * <= 4e9) and returns what the plan reports -- TCFFT_ERR_TIMEOUT when the
+ * bounded wait ran out and the launch skipped the orphaned items.  The
+ * kernel exits normally; the context stays usable.  Allocates and frees its
+ * own buffers; synchronises the device. */
+tcfft_status tcfft_selftest_queue_timeout(long long limit_cycles);
 
 /* Human-readable name of a status code (static string). */
 const char* tcfft_status_string(tcfft_status status);

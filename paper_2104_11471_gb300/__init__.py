@@ -28,6 +28,7 @@ TCFFT_PLAN_INVERSE = 4
 TCFFT_PLAN_SCALE = 8
 TCFFT_PLAN_SHARE_SM = 16  # at most half of each SM's CTA slots (room for other streams)
 TCFFT_PLAN_FUSED_2D = 32  # square 2D up to 512^2: rows and columns in one cluster launch
+TCFFT_PLAN_PERSISTENT = 64  # ragged plans: one persistent launch over a device work queue
 
 STATUS = {
     0: "TCFFT_OK", 1: "TCFFT_ERR_INVALID_SIZE", 2: "TCFFT_ERR_INVALID_VALUE",
@@ -56,6 +57,7 @@ _SIG = {
     "tcfft_plan_describe": (ctypes.c_size_t, [_P, ctypes.c_char_p, ctypes.c_size_t]),
     "tcfft_exec_1d_noalloc": (ctypes.c_int, [_I64, _I64, _P, _P, _P]),
     "tcfft_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_longlong]),
+    "tcfft_selftest_queue_timeout": (ctypes.c_int, [ctypes.c_longlong]),
 }
 
 _lock = threading.Lock()

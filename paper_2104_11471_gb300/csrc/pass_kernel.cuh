@@ -253,7 +253,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // the batch are not copied: their rows only feed outputs that are dropped.
 template <class K>
 __device__ __forceinline__ void issue_raw_copy(const PassParams& p, uint32_t raw_s, uint32_t lbar,
-                                               const uint32_t* gin, int64_t t0, int log2C, int nvalid) {
+                                               const uint32_t* gin, int64_t t0, int log2C, int nvalid,
+                                               const PassParams* maps = nullptr) {
+  const CUtensorMap* in_map = maps ? &maps->in_map : &p.in_map;  // param or global memory
   const uint32_t P = (uint32_t)1 << (log2C + K::LOG2N);
   if constexpr (K::IN_C) {
     if (!p.in_gather) {
@@ -296,7 +298,7 @@ __device__ __forceinline__ void issue_raw_copy(const PassParams& p, uint32_t raw
       const int t3 = (int)(t23 >> p.log2I2);
       for (uint32_t pl = 0; pl < planes; ++pl)
         for (int e0 = 0; e0 < K::N; e0 += bl)
-          tma_load_5d(raw_s + pl * (P * 4u) + (uint32_t)e0 * ((uint32_t)1 << log2C) * 4u * wpp, &p.in_map,
+          tma_load_5d(raw_s + pl * (P * 4u) + (uint32_t)e0 * ((uint32_t)1 << log2C) * 4u * wpp, in_map,
                       (int)t1, e0, t2, t3, (int)pl, lbar);
     }
   } else if (K::SPLIT && p.in_f32) {
@@ -332,7 +334,10 @@ __device__ __forceinline__ void issue_raw_copy(const PassParams& p, uint32_t raw
 // Without FOLD (one radix-16 stage) the twiddle W_N^{k0 n'} is applied here.
 // Source: global memory (SMEM = false; element e of transform c at
 // c*N + e or c + e*es) or the raw shared buffer (SMEM = true; es = C).
-template <class K, bool SMEM>
+// CG: global loads through L2 only (ld.global.cg), for inputs that other CTAs
+// of the same launch wrote (the non-coherent read-only path could return
+// stale lines then).
+template <class K, bool SMEM, bool CG = false>
 __device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, const uint32_t* src,
                                             const uint32_t* src_lo, uint32_t es, int log2C,
                                             int nvalid, int64_t t0 = 0) {
@@ -381,7 +386,7 @@ __device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, con
           if constexpr (SMEM) {
             f = f4[q];
           } else if (valid) {
-            f = __ldg(f4 + q);
+            f = CG ? __ldcg(f4 + q) : __ldg(f4 + q);
           }
           hv[n0][2 * q] = f2h2(f.x, f.y);
           lv[n0][2 * q] = split_lo(f.x, f.y, hv[n0][2 * q]);
@@ -408,8 +413,8 @@ __device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, con
           b = s4[1];
         }
       } else if (valid) {
-        a = __ldg(s4);
-        b = __ldg(s4 + 1);
+        a = CG ? __ldcg(s4) : __ldg(s4);
+        b = CG ? __ldcg(s4 + 1) : __ldg(s4 + 1);
       }
       hv[n0][0] = a.x; hv[n0][1] = a.y; hv[n0][2] = a.z; hv[n0][3] = a.w;
       hv[n0][4] = b.x; hv[n0][5] = b.y; hv[n0][6] = b.z; hv[n0][7] = b.w;
@@ -427,8 +432,8 @@ __device__ __forceinline__ void load_stage1(const PassParams& p, uint8_t* A, con
             d = l4[1];
           }
         } else if (valid) {
-          c2 = __ldg(l4);
-          d = __ldg(l4 + 1);
+          c2 = CG ? __ldcg(l4) : __ldg(l4);
+          d = CG ? __ldcg(l4 + 1) : __ldg(l4 + 1);
         }
         lv[n0][0] = c2.x; lv[n0][1] = c2.y; lv[n0][2] = c2.z; lv[n0][3] = c2.w;
         lv[n0][4] = d.x; lv[n0][5] = d.y; lv[n0][6] = d.z; lv[n0][7] = d.w;
@@ -584,7 +589,8 @@ __device__ __forceinline__ void staging_store(const PassParams& p, uint8_t* A, u
 // the staging copy) or 16-byte stores by every thread.
 template <class K>
 __device__ __forceinline__ void copy_out(const PassParams& p, uint8_t* A, uint32_t* gout, int64_t t0, int nvalid,
-                                         int log2C) {
+                                         int log2C, const PassParams* maps = nullptr) {
+  const CUtensorMap* out_map = maps ? &maps->out_map : &p.out_map;  // param or global memory
   const int tid = threadIdx.x;
   const uint32_t P = (uint32_t)1 << (log2C + K::LOG2N);
   const uint32_t ow = out_words<K>(p);
@@ -598,7 +604,7 @@ __device__ __forceinline__ void copy_out(const PassParams& p, uint8_t* A, uint32
       const uint32_t a0 = smem_u32(A);
       for (int pl = 0; pl < K::PLANES; ++pl)
         for (uint32_t r0 = 0; r0 < (P >> 5); r0 += 256)
-          tma_store_5d(&p.out_map, a0 + (uint32_t)pl * (P * 4u) + r0 * 128u, 0, row0 + (int)r0, pl, 0, 0);
+          tma_store_5d(out_map, a0 + (uint32_t)pl * (P * 4u) + r0 * 128u, 0, row0 + (int)r0, pl, 0, 0);
       bulk_commit();
       bulk_wait_read();  // the staging copy (= A) is rewritten by the next chunk
     }
@@ -630,7 +636,7 @@ __device__ __forceinline__ void copy_out(const PassParams& p, uint8_t* A, uint32
       const uint32_t a0 = smem_u32(A);
       for (int pl = 0; pl < K::PLANES; ++pl)
         for (int e0 = 0; e0 < K::N; e0 += 256)
-          tma_store_5d(&p.out_map, a0 + (uint32_t)pl * (P * 4u) + ((uint32_t)e0 << log2C) * 4u, (int)t1, e0,
+          tma_store_5d(out_map, a0 + (uint32_t)pl * (P * 4u) + ((uint32_t)e0 << log2C) * 4u, (int)t1, e0,
                        t2, t3, pl);
       bulk_commit();
       bulk_wait_read();  // the staging copy (= A) is rewritten by the next chunk
@@ -882,6 +888,197 @@ __device__ __forceinline__ bool run_stages(const PassParams& p, StageCtx& cx, in
   return true;
 }
 
+// Final-stage output of one butterfly of a pass (transform c of the chunk
+// starting at transform t0, output index kbase at k_S = 0): the optional
+// multi-pass output twiddle, the inverse's conjugation, then straight to
+// global memory (DIRECT_OUT) or into the staging copy at A.
+template <class K>
+__device__ __forceinline__ void final_out(const PassParams& p, uint8_t* A, uint32_t* gout, int64_t t0, int nvalid,
+                                          int log2C, uint32_t c, uint32_t kbase, float2 (&X)[8], float2 (&Y)[8]) {
+  const uint32_t ow = out_words<K>(p);
+  constexpr uint32_t kstep = (uint32_t)K::LQ << K::LOG2RX;  // output index step per k_S
+  if (p.otw_level) {
+    // W_M^{col (kbase + kstep k)}: powers of ws = W_M^{col kstep} from
+    // w0 = W_M^{col kbase}, advanced two outputs at a time
+    const int64_t t = t0 + c;
+    const uint32_t col = (p.otw_level == 1)
+                             ? (uint32_t)(t & ((int64_t(1) << p.log2I1) - 1))
+                             : (uint32_t)((t >> p.log2I1) & ((int64_t(1) << p.log2I2) - 1));
+    const float2 w0 = tw_lookup(p.otw_lo, p.otw_hi, col * kbase, p.otw_log2M, p.otw_log2S);
+    const float2 ws = tw_lookup(p.otw_lo, p.otw_hi, col * kstep, p.otw_log2M, p.otw_log2S);
+    const float2 w1 = cmulf(w0, ws), ws2 = cmulf(ws, ws);
+    float2 c2 = make_float2(w0.x, w1.x), d2 = make_float2(w0.y, w1.y);
+    const float2 sc = make_float2(ws2.x, ws2.x), sd = make_float2(ws2.y, ws2.y);
+    const float2 snd = make_float2(-ws2.y, -ws2.y);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      cmul2(X[i], Y[i], c2, d2, make_float2(-d2.x, -d2.y));
+      if (i < 7) {
+        float2 cn = c2, dn = d2;
+        cmul2(cn, dn, sc, sd, snd);
+        c2 = cn;
+        d2 = dn;
+      }
+    }
+  }
+  if (p.conj_out) {
+    // inverse transform: conj() of the result
+#pragma unroll
+    for (int i = 0; i < 8; ++i) Y[i] = make_float2(-Y[i].x, -Y[i].y);
+  }
+  if constexpr (K::DIRECT_OUT) {
+    // lanes hold consecutive output indices: store straight to global
+    if ((int)c < nvalid) {
+      uint32_t* o = (p.out_scatter ? p.out + ow * side_base(p.out_l, t0 + c, p.log2I1, p.log2I2)
+                                   : gout + ow * (c << K::LOG2N)) + ow * kbase;
+      if (K::SPLIT && p.out_f32) {
+        // interleaved FP32 complex straight from the accumulator
+        float2* of = reinterpret_cast<float2*>(o);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          of[(2 * i) * kstep] = make_float2(X[i].x, Y[i].x);
+          of[(2 * i + 1) * kstep] = make_float2(X[i].y, Y[i].y);
+        }
+        return;
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const uint32_t h0 = f2h2(X[i].x, Y[i].x), h1 = f2h2(X[i].y, Y[i].y);
+        o[(2 * i) * kstep] = h0;
+        o[(2 * i + 1) * kstep] = h1;
+        if constexpr (K::SPLIT) {
+          o[p.out_plane + (2 * i) * kstep] = split_lo(X[i].x, Y[i].x, h0);
+          o[p.out_plane + (2 * i + 1) * kstep] = split_lo(X[i].y, Y[i].y, h1);
+        }
+      }
+    }
+    return;
+  }
+  staging_store<K>(p, A, (uint32_t)1 << (log2C + K::LOG2N), log2C, c, kbase, X, Y);
+}
+
+// ------------------------------------------------------------ pass body
+// Per-CTA resources the pass body runs on: the operand area (1 KB aligned:
+// A tiles, raw prefetch buffer and DFT images, laid out per pass), the MMA
+// and copy barriers with their parities, TMEM.
+struct PassCta {
+  uint8_t* A;
+  uint64_t* mbar;
+  uint64_t* lbar;
+  uint32_t tmem;
+  uint32_t phase, lphase;
+};
+
+// Chunks slot, slot + nslots, ... of pass p on this CTA (C transforms each).
+// With async_load, the raw input of the next chunk is copied into shared
+// memory (bulk copy, tensor-map boxes or cp.async) while the current chunk
+// runs its MMA stages, epilogues and stores.  `maps` holds the tensor maps in
+// param or global memory (p may be a shared-memory copy); load_images: copy
+// the pass's DFT images into place first; launch_dependents: trigger the
+// programmatic dependent launch at the CTA's last chunk; CG: synchronous
+// loads through L2 only (inputs written by other CTAs of the same launch).
+// Returns false when a wait timed out (status written); on return no copy
+// targets shared memory and every tensor-map store has completed.
+template <class K, bool CG>
+__device__ __forceinline__ bool pass_body(const PassParams& p, const PassParams& maps, int64_t slot, int64_t nslots,
+                                          PassCta& cta, bool load_images, bool launch_dependents) {
+  const int tid = threadIdx.x;
+  uint8_t* A = cta.A;
+  const int tiles = p.tiles;
+  const int log2C = p.log2C;
+  const int C = 1 << log2C;
+  const uint32_t P = (uint32_t)C << K::LOG2N;  // points per chunk and plane
+  uint8_t* RAW = A + K::PLANES * tiles * kTileBytes;
+  uint8_t* Bs = RAW + (p.async_load ? K::PLANES * P * 4u : 0u);
+  if (load_images) load_dft_images<K>(p, Bs);
+  const uint32_t raw_s = smem_u32(RAW);
+  const uint32_t lbar_s = smem_u32(cta.lbar);
+  const uint32_t* raw32 = reinterpret_cast<const uint32_t*>(RAW);
+  uint32_t lphase = cta.lphase;
+  bool ok = true, pending = false;  // pending: a bulk copy into RAW is in flight
+  StageCtx cx{A, smem_u32(A), smem_u32(Bs), cta.tmem, smem_u32(cta.mbar), cta.phase};
+
+  auto chunk_in = [&](int64_t ch) {
+    return p.in + in_words<K>(p) * side_base(p.in_l, ch << log2C, p.log2I1, p.log2I2);
+  };
+  auto chunk_valid = [&](int64_t ch) {
+    const int64_t left = p.T - (ch << log2C);
+    return left < C ? (int)left : C;
+  };
+
+  int64_t chunk = slot;
+  if (p.async_load && chunk < p.nchunks) {
+    issue_raw_copy<K>(p, raw_s, lbar_s, chunk_in(chunk), chunk << log2C, log2C, chunk_valid(chunk), &maps);
+    pending = K::IN_C || p.in_tma;
+  }
+
+  for (; chunk < p.nchunks; chunk += nslots) {
+    // last chunk of this CTA: the next kernel may start its prologue
+    if (launch_dependents && chunk + nslots >= p.nchunks) griddep_launch_dependents();
+    const int64_t t0 = chunk << log2C;
+    const int nvalid = chunk_valid(chunk);
+    const uint32_t ow = out_words<K>(p);
+    uint32_t* gout = p.out + ow * side_base(p.out_l, t0, p.log2I1, p.log2I2);
+
+    if (p.async_load) {
+      if (K::IN_C || p.in_tma) {
+        // one thread polls the copy's barrier; the others sleep in the CTA
+        // barrier (no issue slots spent spinning) and see the copied bytes
+        // through it
+        bool got = true;
+        if (tid == 0) got = mbar_wait_bounded(lbar_s, lphase, kWaitLimitCycles);
+        if (__syncthreads_or(!got)) {
+          if (tid == 0) atomicExch(p.status, kDevErrTimeout);
+          ok = false;
+          break;
+        }
+        lphase ^= 1u;
+        pending = false;
+      } else {
+        cp_async_wait_all();
+        __syncthreads();
+      }
+      load_stage1<K, true>(p, A, raw32, raw32 + P, K::IN_C ? 1u : (uint32_t)C, log2C, nvalid);
+      __syncthreads();  // raw buffer consumed: prefetch the next chunk into it
+      const int64_t next = chunk + nslots;
+      if (next < p.nchunks) {
+        issue_raw_copy<K>(p, raw_s, lbar_s, chunk_in(next), next << log2C, log2C, chunk_valid(next), &maps);
+        pending = K::IN_C || p.in_tma;
+      }
+    } else {
+      const uint32_t* gin = chunk_in(chunk);
+      load_stage1<K, false, CG>(p, A, gin, gin + p.in_plane, p.in_l.es, log2C, nvalid, t0);
+    }
+
+    fence_proxy_async_smem();
+    tc_fence_before_sync();
+    __syncthreads();
+
+    auto fin = [&](uint32_t c, uint32_t kbase, float2 (&X)[8], float2 (&Y)[8]) {
+      final_out<K>(p, A, gout, t0, nvalid, log2C, c, kbase, X, Y);
+    };
+    ok = run_stages<K>(p, cx, tiles, log2C, fin);
+    if (!ok) break;
+
+    // copy-out: staging (natural order, chunk-swizzled) -> global
+    if constexpr (!K::DIRECT_OUT) copy_out<K>(p, A, gout, t0, nvalid, log2C, &maps);
+    __syncthreads();  // staging (= A) is rewritten by the next chunk
+  }
+
+  if (p.out_tma && tid == 0) bulk_wait_all();
+  // unwind: no copy may still target this CTA's shared memory
+  if (p.async_load) {
+    if (K::IN_C || p.in_tma) {
+      if (pending && mbar_wait_bounded(lbar_s, lphase, kWaitLimitCycles)) lphase ^= 1u;
+    } else {
+      cp_async_wait_all();
+    }
+  }
+  cta.phase = cx.phase;
+  cta.lphase = lphase;
+  return ok;
+}
+
 // ---------------------------------------------------------------- kernel
 // Persistent: CTA b processes chunks b, b + gridDim.x, ... (C transforms
 // each).  With async_load, the raw input of the next chunk is copied into
@@ -923,157 +1120,18 @@ __global__ void __launch_bounds__(kThreads, (PassCfg<LOG2N, MODE, SPLIT>::MINB))
     tmem_relinquish();
   }
 
-  const uint32_t raw_s = smem_u32(RAW);
-  const uint32_t lbar_s = smem_u32(lbar);
-  const uint32_t* raw32 = reinterpret_cast<const uint32_t*>(RAW);
-  uint32_t lphase = 0;
-  bool ok = true, pending = false;  // pending: a bulk copy into RAW is in flight
-
-  auto chunk_in = [&](int64_t ch) {
-    return p.in + in_words<K>(p) * side_base(p.in_l, ch << log2C, p.log2I1, p.log2I2);
-  };
-  auto chunk_valid = [&](int64_t ch) {
-    const int64_t left = p.T - (ch << log2C);
-    return left < C ? (int)left : C;
-  };
-
+  PassCta cta{A, mbar, lbar, 0u, 0u, 0u};
   tc_fence_before_sync();
   __syncthreads();  // barriers initialised, TMEM address published
   tc_fence_after_sync();
-  const uint32_t tmem = *tslot;
-  StageCtx cx{A, smem_u32(A), smem_u32(Bs), tmem, smem_u32(mbar), 0u};
+  cta.tmem = *tslot;
+  const uint32_t tmem = cta.tmem;
 
   // everything above reads only plan-time tables; the pass input may be the
   // previous kernel's output
   griddep_wait();
+  (void)pass_body<K, false>(p, p, blockIdx.x, gridDim.x, cta, false, true);
 
-  int64_t chunk = blockIdx.x;
-  if (p.async_load && chunk < p.nchunks) {
-    issue_raw_copy<K>(p, raw_s, lbar_s, chunk_in(chunk), chunk << log2C, log2C, chunk_valid(chunk));
-    pending = K::IN_C || p.in_tma;
-  }
-
-  for (; chunk < p.nchunks; chunk += gridDim.x) {
-    // last chunk of this CTA: the next kernel may start its prologue
-    if (chunk + gridDim.x >= p.nchunks) griddep_launch_dependents();
-    const int64_t t0 = chunk << log2C;
-    const int nvalid = chunk_valid(chunk);
-    const uint32_t ow = out_words<K>(p);
-    uint32_t* gout = p.out + ow * side_base(p.out_l, t0, p.log2I1, p.log2I2);
-
-    if (p.async_load) {
-      if (K::IN_C || p.in_tma) {
-        // one thread polls the copy's barrier; the others sleep in the CTA
-        // barrier (no issue slots spent spinning) and see the copied bytes
-        // through it
-        bool got = true;
-        if (tid == 0) got = mbar_wait_bounded(lbar_s, lphase, kWaitLimitCycles);
-        if (__syncthreads_or(!got)) {
-          if (tid == 0) atomicExch(p.status, kDevErrTimeout);
-          ok = false;
-          break;
-        }
-        lphase ^= 1u;
-        pending = false;
-      } else {
-        cp_async_wait_all();
-        __syncthreads();
-      }
-      load_stage1<K, true>(p, A, raw32, raw32 + P, K::IN_C ? 1u : (uint32_t)C, log2C, nvalid);
-      __syncthreads();  // raw buffer consumed: prefetch the next chunk into it
-      const int64_t next = chunk + gridDim.x;
-      if (next < p.nchunks) {
-        issue_raw_copy<K>(p, raw_s, lbar_s, chunk_in(next), next << log2C, log2C, chunk_valid(next));
-        pending = K::IN_C || p.in_tma;
-      }
-    } else {
-      const uint32_t* gin = chunk_in(chunk);
-      load_stage1<K, false>(p, A, gin, gin + p.in_plane, p.in_l.es, log2C, nvalid, t0);
-    }
-
-    fence_proxy_async_smem();
-    tc_fence_before_sync();
-    __syncthreads();
-
-    // final stage: transform c of the chunk, output index kbase at k_S = 0
-    auto fin = [&](uint32_t c, uint32_t kbase, float2 (&X)[8], float2 (&Y)[8]) {
-      constexpr uint32_t kstep = (uint32_t)K::LQ << K::LOG2RX;  // output index step per k_S
-      if (p.otw_level) {
-        // W_M^{col (kbase + kstep k)}: powers of ws = W_M^{col kstep} from
-        // w0 = W_M^{col kbase}, advanced two outputs at a time
-        const int64_t t = t0 + c;
-        const uint32_t col = (p.otw_level == 1)
-                                 ? (uint32_t)(t & ((int64_t(1) << p.log2I1) - 1))
-                                 : (uint32_t)((t >> p.log2I1) & ((int64_t(1) << p.log2I2) - 1));
-        const float2 w0 = tw_lookup(p.otw_lo, p.otw_hi, col * kbase, p.otw_log2M, p.otw_log2S);
-        const float2 ws = tw_lookup(p.otw_lo, p.otw_hi, col * kstep, p.otw_log2M, p.otw_log2S);
-        const float2 w1 = cmulf(w0, ws), ws2 = cmulf(ws, ws);
-        float2 c2 = make_float2(w0.x, w1.x), d2 = make_float2(w0.y, w1.y);
-        const float2 sc = make_float2(ws2.x, ws2.x), sd = make_float2(ws2.y, ws2.y);
-        const float2 snd = make_float2(-ws2.y, -ws2.y);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          cmul2(X[i], Y[i], c2, d2, make_float2(-d2.x, -d2.y));
-          if (i < 7) {
-            float2 cn = c2, dn = d2;
-            cmul2(cn, dn, sc, sd, snd);
-            c2 = cn;
-            d2 = dn;
-          }
-        }
-      }
-      if (p.conj_out) {
-        // inverse transform: conj() of the result
-#pragma unroll
-        for (int i = 0; i < 8; ++i) Y[i] = make_float2(-Y[i].x, -Y[i].y);
-      }
-      if constexpr (K::DIRECT_OUT) {
-        // lanes hold consecutive output indices: store straight to global
-        if ((int)c < nvalid) {
-          uint32_t* o = (p.out_scatter ? p.out + ow * side_base(p.out_l, t0 + c, p.log2I1, p.log2I2)
-                                       : gout + ow * (c << K::LOG2N)) + ow * kbase;
-          if (K::SPLIT && p.out_f32) {
-            // interleaved FP32 complex straight from the accumulator
-            float2* of = reinterpret_cast<float2*>(o);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              of[(2 * i) * kstep] = make_float2(X[i].x, Y[i].x);
-              of[(2 * i + 1) * kstep] = make_float2(X[i].y, Y[i].y);
-            }
-            return;
-          }
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const uint32_t h0 = f2h2(X[i].x, Y[i].x), h1 = f2h2(X[i].y, Y[i].y);
-            o[(2 * i) * kstep] = h0;
-            o[(2 * i + 1) * kstep] = h1;
-            if constexpr (K::SPLIT) {
-              o[p.out_plane + (2 * i) * kstep] = split_lo(X[i].x, Y[i].x, h0);
-              o[p.out_plane + (2 * i + 1) * kstep] = split_lo(X[i].y, Y[i].y, h1);
-            }
-          }
-        }
-        return;
-      }
-      staging_store<K>(p, A, (uint32_t)1 << (log2C + K::LOG2N), log2C, c, kbase, X, Y);
-    };
-    ok = run_stages<K>(p, cx, tiles, log2C, fin);
-    if (!ok) break;
-
-    // copy-out: staging (natural order, chunk-swizzled) -> global
-    if constexpr (!K::DIRECT_OUT) copy_out<K>(p, A, gout, t0, nvalid, log2C);
-    __syncthreads();  // staging (= A) is rewritten by the next chunk
-  }
-
-  if (p.out_tma && tid == 0) bulk_wait_all();
-  // unwind: no copy may still target this CTA's shared memory when it exits
-  if (p.async_load) {
-    if (K::IN_C || p.in_tma) {
-      if (pending) (void)mbar_wait_bounded(lbar_s, lphase, kWaitLimitCycles);
-    } else {
-      cp_async_wait_all();
-    }
-  }
   tc_fence_before_sync();
   __syncthreads();
   if (warp == 0) {

@@ -106,6 +106,27 @@ struct Fused2DParams {
   int64_t batch;  // matrices
 };
 
+// A persistent launch over a device work queue (ragged batches): items are
+// (pass, slot) pairs in dependency order -- slot s of a pass runs its chunks
+// s, s + G, ... (G = nchunks[pass] slots); a CTA claims the next item, waits
+// (bounded) until every slot of the pass it depends on is done, runs the slot
+// and counts it done.  Counters are zero at launch.
+struct QueueParams {
+  const PassParams* passes;  // per pass, buffers bound (tensor maps encoded)
+  const int* dep;            // per pass: the pass that must be complete first, or -1
+  const int* nchunks;        // per pass: slots
+  const int2* items;         // (pass, slot)
+  int nitems;
+  int* head;                 // next item to claim
+  int* done;                 // per pass: slots completed
+  int* abort;                // set once a dependency wait timed out: later items are skipped
+  int* status;               // device error word
+  long long wait_limit;      // SM clock cycles a dependency wait may take
+  int a_bytes;               // operand area of the largest pass (A, raw buffer, DFT images)
+  int b_bytes;               // unused (kept 0)
+  int tmem_cols;
+};
+
 constexpr int kTileRows = 128;        // butterflies per MMA tile (M)
 constexpr int kTileBytes = 8192;      // one tile of A: 128 rows x 32 halves
 constexpr int kBImageBytes = 2048;    // 32 x 32 halves, K-major, no swizzle

@@ -74,6 +74,9 @@ struct Fused2DLaunch {
   int regs = 0;
 };
 
+// Kernel entry point of the persistent work-queue executor.
+const void* queue_fn();
+
 // Kernel entry point of the fused 2D pass for S = 2^log2S, or null.
 const void* fused2d_fn(int log2S, bool split);
 

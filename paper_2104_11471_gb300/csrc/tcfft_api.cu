@@ -75,6 +75,27 @@ struct GraphEntry {
   cudaGraphExec_t exec;
 };
 
+// Persistent execution of a ragged plan (TCFFT_PLAN_PERSISTENT): the queue
+// (items, dependencies, chunk counts), its counters and one device copy of
+// the passes' parameters per (in, out) pair.
+struct QueueBinding {
+  const void* in;
+  void* out;
+  PassParams* d_passes;
+};
+struct QueueState {
+  int2* d_items = nullptr;
+  int* d_dep = nullptr;
+  int* d_nchunks = nullptr;
+  int* d_counters = nullptr;  // head, abort, done[passes]
+  int nitems = 0;
+  int a_bytes = 0, b_bytes = 0, tmem_cols = 32;
+  size_t smem = 0;
+  dim3 grid;
+  long long wait_limit = kWaitLimitCycles;
+  std::vector<QueueBinding> bindings;
+};
+
 tcfft_status from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return TCFFT_OK;
   if (e == cudaErrorMemoryAllocation) return TCFFT_ERR_ALLOC;
@@ -114,9 +135,16 @@ struct tcfft_plan_s {
   std::vector<GraphEntry> graphs;     // instantiated graphs by (in, out)
   void* tune_buf = nullptr;           // scratch for autotuning
   size_t tune_bytes = 0;
+  bool queue = false;                 // TCFFT_PLAN_PERSISTENT: one launch over a work queue
+  QueueState q;
 
   ~tcfft_plan_s() {
     for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
+    for (auto& b : q.bindings) cudaFree(b.d_passes);
+    cudaFree(q.d_items);
+    cudaFree(q.d_dep);
+    cudaFree(q.d_nchunks);
+    cudaFree(q.d_counters);
     for (auto* t : toff_tables) cudaFree(t);
     cudaFree(tune_buf);
     for (auto& kv : tables) {
@@ -224,6 +252,17 @@ tcfft_status tune_pass(tcfft_plan_s* pl, Pass& ps, int64_t L, int64_t T, int64_t
                        Side out, int otw_level, int log2M);
 
 PassParams bound_params(const tcfft_plan_s* plan, const Pass& ps, const void* in, void* out);
+
+// Operand area of a pass in shared memory (A tiles, raw prefetch buffer, DFT
+// images) and the cap a persistent queue gives every pass.
+constexpr int64_t kQueueArea = 40 * 1024;
+int64_t queue_area(const Pass& ps) {
+  const int S = ps.p.log2N / 4, RX = 1 << (ps.p.log2N % 4);
+  const int64_t P = int64_t(1) << (ps.p.log2C + ps.p.log2N);
+  return (int64_t)ps.p.tiles * kTileBytes + (ps.p.async_load ? 4 * P : 0) +
+         ((S >= 2 && RX > 1) ? RX : 1) * kBImageBytes;
+}
+
 cudaError_t launch_plan_pass(const tcfft_plan_s* plan, const Pass& ps, const void* in, void* out, cudaStream_t s,
                              int64_t batch = 0);
 
@@ -231,7 +270,31 @@ tcfft_status add_pass(tcfft_plan_s* pl, int64_t L, int64_t T, int64_t I1, int64_
                       Side out, Buf src, Buf dst, int otw_level, int log2M, int group = 0,
                       int64_t src_off = 0, int64_t dst_off = 0) {
   Pass ps;
-  tcfft_status st = pass_geometry(ps, L, T, I1, I2, in, out, pl->split, 0, 0, -1, pl->share_sm);
+  tcfft_status st = TCFFT_ERR_INVALID_SIZE;
+  if (pl->queue) {
+    // passes of a persistent queue share one CTA shape: 128 threads, at most
+    // kQueueArea bytes of operands and 128 TMEM columns (3 CTAs per SM), so
+    // large chunks fall back to smaller ones and then to synchronous loads
+    bool fits = false;
+    for (int64_t tgt : {int64_t(0), int64_t(8192), int64_t(4096), int64_t(2048)}) {
+      for (int as : {-1, 0}) {
+        st = pass_geometry(ps, L, T, I1, I2, in, out, pl->split, tgt, 128, as, pl->share_sm);
+        if (st == TCFFT_OK && queue_area(ps) <= kQueueArea && ps.p.tmem_cols <= 128) {
+          fits = true;
+          break;
+        }
+      }
+      if (fits) break;
+    }
+    if (!fits) {
+      if (env_int("TCFFT_DEBUG", 0))
+        std::fprintf(stderr, "persistent plan: pass of length %lld (T %lld) fits no queue geometry (last %d)\n",
+                     (long long)L, (long long)T, (int)st);
+      return TCFFT_ERR_INVALID_SIZE;
+    }
+  } else {
+    st = pass_geometry(ps, L, T, I1, I2, in, out, pl->split, 0, 0, -1, pl->share_sm);
+  }
   if (st != TCFFT_OK) return st;
   ps.src = src;
   ps.dst = dst;
@@ -240,7 +303,7 @@ tcfft_status add_pass(tcfft_plan_s* pl, int64_t L, int64_t T, int64_t I1, int64_
   ps.group = group;
   st = bind_tables(pl, ps, ilog2(L), otw_level, log2M);
   if (st != TCFFT_OK) return st;
-  if (pl->autotune) {
+  if (!pl->queue && pl->autotune) {
     st = tune_pass(pl, ps, L, T, I1, I2, in, out, otw_level, log2M);
     if (st != TCFFT_OK) return st;
   }
@@ -804,11 +867,13 @@ tcfft_status plan_many(tcfft_plan_s* pl, int64_t count, const int64_t* n0, const
     acc += b ? a * b : a;
   }
   pl->points = acc;
-  const int64_t single = pl->split ? kSingleSplit : kSinglePlain;
+  // persistent queues keep every pass within 8192 points per CTA: longer 1D
+  // transforms run as two passes
+  const int64_t single = pl->queue ? 8192 : (pl->split ? kSingleSplit : kSinglePlain);
   const int64_t cap = pl->split ? kCapSplit : kCapPlain;
   bool need_ws = false;
   for (auto& g : groups)
-    if (g.first.second == 0 && g.first.first > single) need_ws = true;
+    if (g.first.second == 0 && (g.first.first > single || pl->queue)) need_ws = true;
   if (need_ws) {
     pl->ws_bytes = (size_t)acc * 4 * (pl->split ? 2 : 1);
     if (cudaMalloc(&pl->ws, pl->ws_bytes) != cudaSuccess) {
@@ -829,10 +894,14 @@ tcfft_status plan_many(tcfft_plan_s* pl, int64_t count, const int64_t* n0, const
     tcfft_status st;
     if (b == 0) {
       const int64_t n = a;
+      st = TCFFT_ERR_INVALID_SIZE;
       if (n <= single) {
         Side sd{n, 0, 0, 1, toff};
         st = add_pass(pl, n, k, 1, kNoLevel, sd, sd, BUF_IN, BUF_OUT, 0, 0, gid);
-      } else {
+      }
+      // a persistent queue's CTA shape cannot hold every single-pass length
+      // (2048 points: eight transforms per MMA tile): two passes then
+      if (n > single || (st == TCFFT_ERR_INVALID_SIZE && pl->queue)) {
         const int lg = ilog2(n);
         const int64_t N1 = int64_t(1) << ((lg + 1) / 2), N2 = n / N1;
         Side in1{1, 0, 0, N2, toff}, out1{1, n, 0, N2};
@@ -860,8 +929,109 @@ tcfft_status plan_many(tcfft_plan_s* pl, int64_t count, const int64_t* n0, const
   return TCFFT_OK;
 }
 
+// The work queue of a persistent plan: items (pass, slot) level by level
+// (every slot of the first pass of every group, then of the second, ...),
+// each pass depending on the previous pass of its group; counters, geometry
+// of the launch.  A slot runs the chunks slot, slot + G, ... of its pass (G =
+// the pass's slots = min(chunks, the launch's CTAs)).
+tcfft_status build_queue(tcfft_plan_s* pl) {
+  QueueState& q = pl->q;
+  const int np = (int)pl->passes.size();
+  std::vector<int> dep(np, -1), nslot(np), level(np, 0);
+  int maxlevel = 0;
+  for (int i = 0; i < np; ++i) {
+    const Pass& ps = pl->passes[i];
+    if (ps.fused || pl->split) return TCFFT_ERR_UNSUPPORTED;
+    if (i > 0 && pl->passes[i - 1].group == ps.group) {
+      dep[i] = i - 1;
+      level[i] = level[i - 1] + 1;
+    }
+    maxlevel = std::max(maxlevel, level[i]);
+    // the pass body's operand area: A tiles, raw prefetch buffer, DFT images
+    q.a_bytes = (int)std::max<int64_t>(q.a_bytes, (queue_area(ps) + 1023) & ~int64_t(1023));
+    q.tmem_cols = std::max(q.tmem_cols, ps.p.tmem_cols);
+  }
+  q.b_bytes = 0;
+  // one CTA shape for every pass: 128 threads, the largest operand area and
+  // TMEM allocation; CTAs per SM from the launch bounds (4), shared memory
+  // and TMEM
+  const void* fn = queue_fn();
+  q.smem = 1008 + (size_t)q.a_bytes + sizeof(PassParams) + 64;
+  if (q.smem > 227 * 1024) return TCFFT_ERR_INVALID_SIZE;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess ||
+      cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
+    return TCFFT_ERR_CUDA;
+  int dev = 0, sms = 1, smem_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  const int occ = std::max(1, std::min(std::min(4, 512 / q.tmem_cols), smem_sm / (int)(q.smem + 1024)));
+  const int64_t ctas = (int64_t)occ * sms;
+  std::vector<int2> items;
+  for (int i = 0; i < np; ++i) nslot[i] = (int)std::min<int64_t>(pl->passes[i].p.nchunks, ctas);
+  for (int lv = 0; lv <= maxlevel; ++lv)
+    for (int i = 0; i < np; ++i)
+      if (level[i] == lv)
+        for (int c = 0; c < nslot[i]; ++c) items.push_back(make_int2(i, c));
+  q.nitems = (int)items.size();
+  q.grid = dim3((unsigned)std::min<int64_t>(ctas, q.nitems));
+  if (cudaMalloc(&q.d_items, sizeof(int2) * items.size()) != cudaSuccess ||
+      cudaMalloc(&q.d_dep, sizeof(int) * np) != cudaSuccess || cudaMalloc(&q.d_nchunks, sizeof(int) * np) != cudaSuccess ||
+      cudaMalloc(&q.d_counters, sizeof(int) * (2 + np)) != cudaSuccess)
+    return TCFFT_ERR_ALLOC;
+  if (cudaMemcpy(q.d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(q.d_dep, dep.data(), sizeof(int) * np, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(q.d_nchunks, nslot.data(), sizeof(int) * np, cudaMemcpyHostToDevice) != cudaSuccess)
+    return TCFFT_ERR_CUDA;
+  return TCFFT_OK;
+}
+
+// Runs a persistent plan: counters to zero, then one launch of the queue
+// kernel over the passes' parameters bound to (in, out).
+tcfft_status exec_queue(tcfft_plan_s* plan, const void* in, void* out, cudaStream_t s) {
+  QueueState& q = plan->q;
+  PassParams* d_passes = nullptr;
+  for (const QueueBinding& b : q.bindings)
+    if (b.in == in && b.out == out) d_passes = b.d_passes;
+  if (!d_passes) {
+    std::vector<PassParams> hp;
+    for (const Pass& ps : plan->passes) hp.push_back(bound_params(plan, ps, in, out));
+    if (cudaMalloc(&d_passes, sizeof(PassParams) * hp.size()) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return TCFFT_ERR_ALLOC;
+    }
+    if (cudaMemcpy(d_passes, hp.data(), sizeof(PassParams) * hp.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(d_passes);
+      return TCFFT_ERR_CUDA;
+    }
+    if (q.bindings.size() >= 8) {  // keep a few buffer pairs
+      cudaFree(q.bindings.front().d_passes);
+      q.bindings.erase(q.bindings.begin());
+    }
+    q.bindings.push_back(QueueBinding{in, out, d_passes});
+  }
+  const int np = (int)plan->passes.size();
+  if (cudaMemsetAsync(q.d_counters, 0, sizeof(int) * (2 + np), s) != cudaSuccess) return TCFFT_ERR_CUDA;
+  QueueParams qp;
+  qp.passes = d_passes;
+  qp.dep = q.d_dep;
+  qp.nchunks = q.d_nchunks;
+  qp.items = q.d_items;
+  qp.nitems = q.nitems;
+  qp.head = q.d_counters;
+  qp.abort = q.d_counters + 1;
+  qp.done = q.d_counters + 2;
+  qp.status = plan->d_status;
+  qp.wait_limit = q.wait_limit;
+  qp.a_bytes = q.a_bytes;
+  qp.b_bytes = q.b_bytes;
+  qp.tmem_cols = q.tmem_cols;
+  void* args[1] = {&qp};
+  return launch_pass(queue_fn(), q.grid, 128, q.smem, s, args) == cudaSuccess ? TCFFT_OK : TCFFT_ERR_LAUNCH;
+}
+
 constexpr unsigned kPlanFlags = TCFFT_PLAN_AUTOTUNE | TCFFT_PLAN_GRAPH | TCFFT_PLAN_INVERSE | TCFFT_PLAN_SCALE |
-                                TCFFT_PLAN_SHARE_SM | TCFFT_PLAN_FUSED_2D;
+                                TCFFT_PLAN_SHARE_SM | TCFFT_PLAN_FUSED_2D | TCFFT_PLAN_PERSISTENT;
 
 void apply_flags(tcfft_plan_s* pl, unsigned flags) {
   pl->autotune = (flags & TCFFT_PLAN_AUTOTUNE) || env_int("TCFFT_AUTOTUNE", 0);
@@ -1123,6 +1293,39 @@ tcfft_status tcfft_selftest_wait_timeout(long long limit_cycles) {
   return (tcfft_status)v;
 }
 
+tcfft_status tcfft_selftest_queue_timeout(long long limit_cycles) {
+  if (limit_cycles < 0 || limit_cycles > 4000000000LL) return TCFFT_ERR_INVALID_VALUE;
+  // a persistent plan of one two-pass transform whose queue keeps only the
+  // second pass's items: their producer is never enqueued, so the first
+  // dependency wait runs out
+  const int64_t n0[1] = {int64_t(1) << 16};
+  tcfft_plan pl = nullptr;
+  tcfft_status st = tcfft_plan_many(&pl, 1, n0, nullptr, TCFFT_FP16, TCFFT_PLAN_PERSISTENT);
+  if (st != TCFFT_OK) return st;
+  void* buf = nullptr;
+  QueueState& q = pl->q;
+  std::vector<int2> items(q.nitems);
+  st = TCFFT_ERR_CUDA;
+  if (pl->passes.size() == 2 &&
+      cudaMemcpy(items.data(), q.d_items, sizeof(int2) * items.size(), cudaMemcpyDeviceToHost) == cudaSuccess) {
+    std::vector<int2> kept;
+    for (const int2& it : items)
+      if (it.x == 1) kept.push_back(it);
+    if (!kept.empty() && cudaMemcpy(q.d_items, kept.data(), sizeof(int2) * kept.size(), cudaMemcpyHostToDevice) ==
+                             cudaSuccess &&
+        cudaMalloc(&buf, pl->io_bytes()) == cudaSuccess && cudaMemset(buf, 0, pl->io_bytes()) == cudaSuccess) {
+      q.nitems = (int)kept.size();
+      q.wait_limit = limit_cycles;
+      st = exec_queue(pl, buf, buf, nullptr);
+      if (st == TCFFT_OK) st = tcfft_plan_last_error(pl);
+    }
+  }
+  cudaFree(buf);
+  tcfft_destroy(pl);
+  (void)cudaGetLastError();
+  return st;
+}
+
 tcfft_status tcfft_plan_1d_ex(tcfft_plan* plan, int64_t n, int64_t batch, tcfft_precision precision,
                               unsigned flags) {
   if (!plan) return TCFFT_ERR_INVALID_VALUE;
@@ -1205,10 +1408,15 @@ tcfft_status tcfft_plan_many(tcfft_plan* plan, int64_t count, const int64_t* n0,
   pl->batch = count;
   set_precision(pl, precision);
   apply_flags(pl, flags);
+  // TCFFT_PLAN_PERSISTENT: plain FP16 ragged plans run as one persistent
+  // launch over a work queue (other precisions keep one launch per pass)
+  pl->queue = (flags & TCFFT_PLAN_PERSISTENT) && precision == TCFFT_FP16;
+  if (pl->queue) pl->fused_2d = false;
   st = common_init(pl);
   if (st == TCFFT_OK) st = plan_many(pl, count, n0, n1);
   if (st == TCFFT_OK) apply_direction(pl);
   if (st == TCFFT_OK) apply_io(pl);
+  if (st == TCFFT_OK && pl->queue) st = build_queue(pl);
   return finish(pl, st, plan);
 }
 
@@ -1221,6 +1429,7 @@ tcfft_status tcfft_exec(tcfft_plan plan, const void* in, void* out, void* stream
   if ((reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(out) & 15))
     return TCFFT_ERR_INVALID_VALUE;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (plan->queue) return exec_queue(plan, in, out, s);
   if (plan->use_graph) return exec_graph(plan, in, out, s);
   for (const Pass& ps : plan->passes) {
     cudaError_t e = launch_plan_pass(plan, ps, in, out, s);
@@ -1353,7 +1562,10 @@ size_t tcfft_workspace_bytes(tcfft_plan plan) {
   return b;
 }
 
-int tcfft_plan_num_launches(tcfft_plan plan) { return plan ? (int)plan->passes.size() : 0; }
+int tcfft_plan_num_launches(tcfft_plan plan) {
+  if (!plan) return 0;
+  return plan->queue ? 1 : (int)plan->passes.size();
+}
 
 size_t tcfft_plan_describe(tcfft_plan plan, char* buf, size_t len) {
   if (!plan) return 0;
@@ -1368,10 +1580,10 @@ size_t tcfft_plan_describe(tcfft_plan plan, char* buf, size_t len) {
                   "%s{\"log2n\": %d, \"mode\": \"%s\", \"transforms\": %lld, \"per_cta\": %d, "
                   "\"tiles\": %d, \"tmem_cols\": %d, \"smem\": %zu, \"async_load\": %d, \"grid\": %u, "
                   "\"chunks\": %lld, \"out_twiddle\": %d, \"ctas_per_sm\": %d, \"regs\": %d, "
-                  "\"threads\": %d, \"cluster\": %d}",
+                  "\"threads\": %d, \"cluster\": %d, \"queue\": %d}",
                   i ? ", " : "", p.log2N, modes[mode], (long long)p.T, 1 << p.log2C, p.tiles, p.tmem_cols,
                   ps.smem, p.async_load, ps.grid.x, (long long)p.nchunks, p.otw_level, ps.occ, ps.regs,
-                  ps.threads, 1 << ps.log2K);
+                  ps.threads, 1 << ps.log2K, plan->queue ? 1 : 0);
     out += tmp;
   }
   out += "]";

@@ -45,7 +45,7 @@ def test_argument_checks_before_device(lib):
     for nx, ny in ((16, 8), (8192 * 2, 16), (48, 64)):
         assert lib.tcfft_plan_2d(ctypes.byref(h), nx, ny, 1) == 1
     assert lib.tcfft_plan_1d_ex(ctypes.byref(h), 256, 1, 7, 0) == 2   # bad precision
-    assert lib.tcfft_plan_1d_ex(ctypes.byref(h), 256, 1, 0, 64) == 2  # unknown flag bit
+    assert lib.tcfft_plan_1d_ex(ctypes.byref(h), 256, 1, 0, 1 << 10) == 2  # unknown flag bit
     a = (ctypes.c_int64 * 2)(256, 100)
     assert lib.tcfft_plan_many(ctypes.byref(h), 2, a, None, 0, 0) == 1  # 100 is not a power of two
     b = (ctypes.c_int64 * 1)(1 << 25)
