@@ -23,11 +23,12 @@ Admission counts everything the server holds on the device against the HBM
 budget: the input pool, every resident plan's own memory (workspace, twiddle
 tables, DFT-matrix images: tcfft_workspace_bytes) and the input and output
 buffers of the batches in flight.  A request whose plan is not resident
-brings the plan's estimated bytes with it; when the total would pass the
-budget, idle plans (no batch in flight) are destroyed, least recently used
-first, and a new plan that still does not fit is made for fewer transforms
-(its capacity halved down to the batch at hand).  Otherwise the request
-waits until running batches free memory.
+brings the plan's estimated bytes with it.  When the total would pass the
+budget the request waits until running batches free memory; only when the
+resident set alone leaves no room are idle plans (no batch in flight)
+destroyed, least recently used first (re-creating a plan synchronises the
+device), and a new plan that still does not fit is made for fewer
+transforms (its capacity halved down to the batch at hand).
 
 Latency is arrival to completion as seen by the host.  All transform work
 runs in libtcfft's kernels; this module only schedules, allocates and copies.
@@ -174,7 +175,7 @@ class FFTServer:
 
     def _evict_idle(self, need: int, keep) -> None:
         """Destroys idle plans (no batch in flight), least recently used
-        first, until `need` more bytes fit the budget."""
+        first, until `need` more bytes fit the budget beside what is in use."""
         idle = sorted((k for k in self.plan_bytes if k != keep and not self.plan_jobs.get(k)),
                       key=lambda k: self.plan_used.get(k, -1))
         for k in idle:
@@ -239,11 +240,15 @@ class FFTServer:
         nbytes = 2 * planes * total * m * 4
         need = nbytes + plan_need
         if self.resident_bytes() + self.in_use + need > self.budget:
-            self._evict_idle(need, keep=key)
-        if self.resident_bytes() + self.in_use + need > self.budget:
-            if not inflight:
-                raise RuntimeError("request larger than the HBM budget")
-            return None
+            # running batches free their memory soon: wait for them, unless
+            # the resident set alone leaves no room (then evict idle plans;
+            # re-creating an evicted plan synchronises the device)
+            if self.resident_bytes() + need > self.budget:
+                self._evict_idle(need - self.in_use, keep=key)
+            if self.resident_bytes() + self.in_use + need > self.budget:
+                if not inflight:
+                    raise RuntimeError("request larger than the HBM budget")
+                return None
         if not resident:
             self.ensure_plan(shape, split, cap)
         return group, nbytes
