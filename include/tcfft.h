@@ -165,26 +165,32 @@ tcfft_status tcfft_exec_batch(tcfft_plan plan, const void* in, void* out, int64_
  * are allocated on the first call. */
 tcfft_status tcfft_exec_host(tcfft_plan plan, const void* host_in, void* host_out, void* stream);
 
-/* Frees everything the plan owns.  NULL is accepted. */
+/* Frees everything the plan owns (no counterpart in the paper: plan
+ * lifetime is library plumbing).  NULL is accepted. */
 tcfft_status tcfft_destroy(tcfft_plan plan);
 
 /* Reads and clears the plan's device status word (synchronises the device
- * first).  TCFFT_OK when no kernel reported an error. */
+ * first).  TCFFT_OK when no kernel reported an error.  No counterpart in the
+ * paper: it reports the bounded device-side waits and launch checks of this
+ * library. */
 tcfft_status tcfft_plan_last_error(tcfft_plan plan);
 
-/* Bytes of one input (== output) buffer of the plan. */
+/* Bytes of one input (== output) buffer of the plan (no counterpart in the
+ * paper; follows from the plan's sizes and precision). */
 size_t tcfft_io_bytes(tcfft_plan plan);
 
 /* Device memory the plan holds besides the caller's buffers (workspace,
- * tables, host-path staging); for admission control. */
+ * tables, host-path staging); for admission control (no counterpart in the
+ * paper). */
 size_t tcfft_workspace_bytes(tcfft_plan plan);
 
-/* Number of kernel launches one tcfft_exec issues. */
+/* Number of kernel launches one tcfft_exec issues (no counterpart in the
+ * paper; the launches are the merging passes of Sec. 3.1). */
 int tcfft_plan_num_launches(tcfft_plan plan);
 
 /* Writes a JSON description of the plan's kernel launches (length, layout
  * mode, transforms per CTA, tiles, TMEM columns, shared memory, grid) into
- * buf (at most len bytes, NUL-terminated).  Returns the length the full
+ * buf (at most len bytes, NUL-terminated; no counterpart in the paper).  Returns the length the full
  * description needs, including the NUL; 0 for a NULL plan. */
 size_t tcfft_plan_describe(tcfft_plan plan, char* buf, size_t len);
 
@@ -213,11 +219,12 @@ size_t tcfft_plan_describe(tcfft_plan plan, char* buf, size_t len);
  * it reads).  Device-side wait timeouts of these kernels are not reported. */
 tcfft_status tcfft_exec_1d_noalloc(int64_t n, int64_t batch, const void* in, void* out, void* stream);
 
-/* Failure-path self-test: runs one kernel that waits, with the library's
- * bounded device-side wait, on a barrier that nothing ever completes, and
- * returns what the kernel reports -- TCFFT_ERR_TIMEOUT once limit_cycles
- * (SM clock cycles, <= 4e9) have passed.  The kernel exits normally; the
- * context stays usable.  Synchronises the device. */
+/* Failure-path self-test (no counterpart in the paper): runs one kernel
+ * that waits, with the library's bounded device-side wait, on a barrier
+ * that nothing ever completes, and returns what the kernel reports --
+ * TCFFT_ERR_TIMEOUT once limit_cycles (SM clock cycles, <= 4e9) have
+ * passed.  The kernel exits normally; the context stays usable.
+ * Synchronises the device. */
 tcfft_status tcfft_selftest_wait_timeout(long long limit_cycles);
 
 /* Failure-path self-test of the persistent executor (TCFFT_PLAN_PERSISTENT;
@@ -230,7 +237,8 @@ tcfft_status tcfft_selftest_wait_timeout(long long limit_cycles);
  * own buffers; synchronises the device. */
 tcfft_status tcfft_selftest_queue_timeout(long long limit_cycles);
 
-/* Human-readable name of a status code (static string). */
+/* Human-readable name of a status code (static string; no counterpart in
+ * the paper). */
 const char* tcfft_status_string(tcfft_status status);
 
 #ifdef __cplusplus
