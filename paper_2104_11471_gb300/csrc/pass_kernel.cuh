@@ -589,7 +589,7 @@ __device__ __forceinline__ void staging_store(const PassParams& p, uint8_t* A, u
 // the staging copy) or 16-byte stores by every thread.
 template <class K>
 __device__ __forceinline__ void copy_out(const PassParams& p, uint8_t* A, uint32_t* gout, int64_t t0, int nvalid,
-                                         int log2C, const PassParams* maps = nullptr) {
+                                         int log2C, const PassParams* maps = nullptr, bool wait_read = true) {
   const CUtensorMap* out_map = maps ? &maps->out_map : &p.out_map;  // param or global memory
   const int tid = threadIdx.x;
   const uint32_t P = (uint32_t)1 << (log2C + K::LOG2N);
@@ -606,7 +606,7 @@ __device__ __forceinline__ void copy_out(const PassParams& p, uint8_t* A, uint32
         for (uint32_t r0 = 0; r0 < (P >> 5); r0 += 256)
           tma_store_5d(out_map, a0 + (uint32_t)pl * (P * 4u) + r0 * 128u, 0, row0 + (int)r0, pl, 0, 0);
       bulk_commit();
-      bulk_wait_read();  // the staging copy (= A) is rewritten by the next chunk
+      if (wait_read) bulk_wait_read();  // the staging copy (= A) is rewritten by the next chunk
     }
   } else if constexpr (K::OUT_C) {
     const uint32_t vchunks = ((uint32_t)nvalid << K::LOG2N) >> 2;
@@ -639,7 +639,7 @@ __device__ __forceinline__ void copy_out(const PassParams& p, uint8_t* A, uint32
           tma_store_5d(out_map, a0 + (uint32_t)pl * (P * 4u) + ((uint32_t)e0 << log2C) * 4u, (int)t1, e0,
                        t2, t3, pl);
       bulk_commit();
-      bulk_wait_read();  // the staging copy (= A) is rewritten by the next chunk
+      if (wait_read) bulk_wait_read();  // the staging copy (= A) is rewritten by the next chunk
     }
   } else {
     const int cq = log2C - 2;  // log2 of the chunks per output element index
@@ -1026,7 +1026,10 @@ __device__ __forceinline__ bool pass_body(const PassParams& p, const PassParams&
         // barrier (no issue slots spent spinning) and see the copied bytes
         // through it
         bool got = true;
-        if (tid == 0) got = mbar_wait_bounded(lbar_s, lphase, kWaitLimitCycles);
+        if (tid == 0) {
+          got = mbar_wait_bounded(lbar_s, lphase, kWaitLimitCycles);
+          if (p.out_tma) bulk_wait_read();  // the previous chunk's stores have read the staging copy (= A)
+        }
         if (__syncthreads_or(!got)) {
           if (tid == 0) atomicExch(p.status, kDevErrTimeout);
           ok = false;
@@ -1036,6 +1039,7 @@ __device__ __forceinline__ bool pass_body(const PassParams& p, const PassParams&
         pending = false;
       } else {
         cp_async_wait_all();
+        if (tid == 0 && p.out_tma) bulk_wait_read();
         __syncthreads();
       }
       load_stage1<K, true>(p, A, raw32, raw32 + P, K::IN_C ? 1u : (uint32_t)C, log2C, nvalid);
@@ -1060,8 +1064,11 @@ __device__ __forceinline__ bool pass_body(const PassParams& p, const PassParams&
     ok = run_stages<K>(p, cx, tiles, log2C, fin);
     if (!ok) break;
 
-    // copy-out: staging (natural order, chunk-swizzled) -> global
-    if constexpr (!K::DIRECT_OUT) copy_out<K>(p, A, gout, t0, nvalid, log2C, &maps);
+    // copy-out: staging (natural order, chunk-swizzled) -> global.  With
+    // prefetching, the wait for the tensor-map stores to read the staging
+    // copy moves to the next chunk's input wait, just before load_stage1
+    // rewrites A, so the issuing thread does not poll for it here.
+    if constexpr (!K::DIRECT_OUT) copy_out<K>(p, A, gout, t0, nvalid, log2C, &maps, !p.async_load);
     __syncthreads();  // staging (= A) is rewritten by the next chunk
   }
 
