@@ -49,6 +49,10 @@ constexpr int64_t kCapSplit = 16384;
 // largest single-pass transform (contiguous side)
 constexpr int64_t kSinglePlain = 16384;
 constexpr int64_t kSingleSplit = 16384;
+// largest single-pass 1D plan in split precision: a 16384-point split pass
+// holds one CTA per SM (shared memory), and 32 x 512 in two passes is faster
+// (2^28 points: 2.01 ms against 2.19 ms)
+constexpr int64_t kSingleSplit1D = 8192;
 
 enum Buf { BUF_IN = 0, BUF_OUT = 1, BUF_WS = 2 };
 
@@ -653,7 +657,7 @@ std::vector<std::vector<int>> split_candidates(const tcfft_plan_s* pl, int lg) {
 }
 
 // The split the planner takes without autotuning (measured at 2^28 points):
-// one pass to 16384; two passes N1 x N2, N1 = 2^ceil(lg/2), to 2^21; three
+// one pass to 16384 (split precision: to 8192); two passes N1 x N2, N1 = 2^ceil(lg/2), to 2^21; three
 // passes from 2^22 (tuning override TCFFT_THREE_PASS_MIN), always beyond
 // 2^24 and for split precision beyond 2^22 (the four-step split would need
 // strided passes longer than the split kernels' 2^11).  2^22 as 16 x 512 x
@@ -668,13 +672,14 @@ std::vector<int> default_split(const tcfft_plan_s* pl, int lg) {
     const int l2 = (lg - l1 + 1) / 2;
     return {l1, l2, lg - l1 - l2};
   }
-  const int l1 = env_int("TCFFT_FOUR_STEP_L1", (lg + 1) / 2);  // tuning override
+  // split 2^14: 32 x 512, the autotuner's pick among 32 x 512 ... 512 x 32
+  const int l1 = env_int("TCFFT_FOUR_STEP_L1", (pl->split && lg == 14) ? 5 : (lg + 1) / 2);  // tuning override
   return {l1, lg - l1};
 }
 
 tcfft_status plan_1d(tcfft_plan_s* pl) {
   const int64_t n = pl->n, B = pl->batch;
-  const int64_t single = std::min<int64_t>(pl->split ? kSingleSplit : kSinglePlain,
+  const int64_t single = std::min<int64_t>(pl->split ? kSingleSplit1D : kSinglePlain,
                                            int64_t(1) << env_int("TCFFT_SINGLE_MAX_LOG2", 14));  // tuning override
   const int lg = ilog2(n);
   if (n <= single) {

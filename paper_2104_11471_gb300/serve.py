@@ -150,12 +150,12 @@ class FFTServer:
 
     def plan_estimate(self, shape, split: bool, cap: int) -> int:
         """Device bytes a plan for `cap` transforms will hold: the multi-pass
-        workspace (1D beyond 16384 points, 2D columns beyond 2048 rows) plus
-        a margin for its tables and images (well under 1 MiB up to 2^20
-        points)."""
+        workspace (1D beyond 16384 points, 8192 in split precision; 2D
+        columns beyond 2048 rows) plus a margin for its tables and images
+        (well under 1 MiB up to 2^20 points)."""
         m = int(np.prod(shape))
         planes = 2 if split else 1
-        multi = m > 16384 if len(shape) == 1 else shape[0] > 2048
+        multi = m > (8192 if split else 16384) if len(shape) == 1 else shape[0] > 2048
         return (cap * m * 4 * planes if multi else 0) + (1 << 20)
 
     def _create_plan(self, shape, split: bool, cap: int):
