@@ -187,8 +187,10 @@ __device__ __forceinline__ void a_store8c(uint8_t* A, uint32_t m0, uint32_t k,
                               __byte_perm(v[4], v[5], 0x5410), __byte_perm(v[6], v[7], 0x5410));
   const uint4 im = make_uint4(__byte_perm(v[0], v[1], 0x7632), __byte_perm(v[2], v[3], 0x7632),
                               __byte_perm(v[4], v[5], 0x7632), __byte_perm(v[6], v[7], 0x7632));
-  *reinterpret_cast<uint4*>(A + a_off(m0, k)) = re;
-  *reinterpret_cast<uint4*>(A + a_off(m0, 16 + k)) = im;
+  // K = 16 + k lies two K-atoms (2048 bytes) after K = k, same swizzle phase
+  uint8_t* a = A + a_off(m0, k);
+  *reinterpret_cast<uint4*>(a) = re;
+  *reinterpret_cast<uint4*>(a + 2048) = im;
 }
 
 // Staging-buffer swizzle for the final stage.  Output word (c, ko) of the
@@ -561,25 +563,36 @@ __device__ __forceinline__ void staging_store(const PassParams& p, uint8_t* A, u
     if (p.out_tma) key = ((base >> 5) & ((1u << (log2C - 2)) - 1u)) << 2;
   }
   const uint32_t wstep = K::OUT_C ? kstep : (kstep << log2C);
+  // The key changes bits 2..4 of the word index only, so with a step that is
+  // a multiple of 32 words (base + n step) ^ key = (base ^ key) + n step: the
+  // 16 stores then share one address and differ by constant offsets.  Taken
+  // where the step is a compile-time constant (contiguous output); with the
+  // run-time step of strided output it measured slower for 1024-point passes.
+  auto put = [&](uint32_t* s0, auto idx) {
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const uint32_t i0 = (base + (2 * i) * wstep) ^ key;
-    const uint32_t i1 = (base + (2 * i + 1) * wstep) ^ key;
-    if (K::SPLIT && p.out_f32) {
-      // FP32 output: the two staging planes hold re and im
-      stg[i0] = __float_as_uint(X[i].x);
-      stg[i1] = __float_as_uint(X[i].y);
-      stg[P + i0] = __float_as_uint(Y[i].x);
-      stg[P + i1] = __float_as_uint(Y[i].y);
-      continue;
+    for (int i = 0; i < 8; ++i) {
+      const uint32_t i0 = idx(2 * i), i1 = idx(2 * i + 1);
+      if (K::SPLIT && p.out_f32) {
+        // FP32 output: the two staging planes hold re and im
+        s0[i0] = __float_as_uint(X[i].x);
+        s0[i1] = __float_as_uint(X[i].y);
+        s0[P + i0] = __float_as_uint(Y[i].x);
+        s0[P + i1] = __float_as_uint(Y[i].y);
+        continue;
+      }
+      const uint32_t h0 = f2h2(X[i].x, Y[i].x), h1 = f2h2(X[i].y, Y[i].y);
+      s0[i0] = h0;
+      s0[i1] = h1;
+      if constexpr (K::SPLIT) {
+        s0[P + i0] = split_lo(X[i].x, Y[i].x, h0);
+        s0[P + i1] = split_lo(X[i].y, Y[i].y, h1);
+      }
     }
-    const uint32_t h0 = f2h2(X[i].x, Y[i].x), h1 = f2h2(X[i].y, Y[i].y);
-    stg[i0] = h0;
-    stg[i1] = h1;
-    if constexpr (K::SPLIT) {
-      stg[P + i0] = split_lo(X[i].x, Y[i].x, h0);
-      stg[P + i1] = split_lo(X[i].y, Y[i].y, h1);
-    }
+  };
+  if constexpr (K::OUT_C && (kstep & 31u) == 0u) {
+    put(stg + (base ^ key), [&](int n) { return (uint32_t)n * kstep; });
+  } else {
+    put(stg, [&](int n) { return (base + (uint32_t)n * wstep) ^ key; });
   }
 }
 
