@@ -566,8 +566,9 @@ __device__ __forceinline__ void staging_store(const PassParams& p, uint8_t* A, u
   // The key changes bits 2..4 of the word index only, so with a step that is
   // a multiple of 32 words (base + n step) ^ key = (base ^ key) + n step: the
   // 16 stores then share one address and differ by constant offsets.  Taken
-  // where the step is a compile-time constant (contiguous output); with the
-  // run-time step of strided output it measured slower for 1024-point passes.
+  // where the step is a compile-time constant (contiguous output) and for
+  // the strided output of 256-point passes (step 16 C); for 512- and
+  // 1024-point passes with their run-time step it measured slower.
   auto put = [&](uint32_t* s0, auto idx) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -591,6 +592,8 @@ __device__ __forceinline__ void staging_store(const PassParams& p, uint8_t* A, u
   };
   if constexpr (K::OUT_C && (kstep & 31u) == 0u) {
     put(stg + (base ^ key), [&](int n) { return (uint32_t)n * kstep; });
+  } else if (!K::OUT_C && K::LOG2N == 8 && (wstep & 31u) == 0u) {
+    put(stg + (base ^ key), [&](int n) { return ((uint32_t)n * kstep) << log2C; });
   } else {
     put(stg, [&](int n) { return (base + (uint32_t)n * wstep) ^ key; });
   }
