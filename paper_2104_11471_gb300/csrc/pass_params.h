@@ -45,9 +45,9 @@ struct PassParams {
   int64_t T;            // transforms in the pass
   int log2I1, log2I2;
   SideLayout in_l, out_l;
-  // Per-stage twiddle bases for radix-16 stages 1..S-1: entry (j, nrest) is
-  // (w, w^2), w = W_{L_j}^{nrest}, L_j = 16^{S-j+1}; stage j starts at entry
-  // sum_{i<j} 16^{S-i}.
+  // Epilogue twiddles of radix-16 stages 1..S-1 (stage_twiddle_kernel): one
+  // float4 (a, b) per row key, then 8 float4 per key holding its 16
+  // twiddles a b^k as packed pairs.
   const float4* stw;
   // W_N table for this pass (factored: W_N^a = hi[a >> log2S] * lo[a & (S-1)])
   const float* tw_lo;   // float2 pairs
@@ -130,6 +130,7 @@ struct QueueParams {
 constexpr int kTileRows = 128;        // butterflies per MMA tile (M)
 constexpr int kTileBytes = 8192;      // one tile of A: 128 rows x 32 halves
 constexpr int kBImageBytes = 2048;    // 32 x 32 halves, K-major, no swizzle
+constexpr int kStageSlots = 9;        // float4 entries per epilogue-twiddle key: (a, b) and 8 twiddle pairs
 constexpr int kThreads = 256;        // 8 warps: two per TMEM lane quarter
 constexpr long long kWaitLimitCycles = 2000000000LL;  // ~1 s at 2 GHz
 

@@ -25,39 +25,55 @@ static __global__ void twiddle_table_kernel(float2* lo, float2* hi, int log2M, i
 }
 
 // Epilogue twiddles of a pass of length N = RX * 16^S (L = 16^S, LQ = L/16):
-// the twiddle of output k of a butterfly row is a * b^k with one float4
-// entry (a, b) per row key:
-//   stage 1, entry k0 * LQ + nrest (k0 < RX, nrest < LQ):
-//       a = W_N^{k0 nrest}, b = W_L^{nrest}
-//   stage j = 2..S-1, entry RX*LQ + sum_{2<=i<j} 16^{S-i} + nrest:
+// the twiddle of output k of a butterfly row is a * b^k, per row key
+//   stage 1, key k0 * LQ + nrest (k0 < RX, nrest < LQ):
+//       a = W_N^{k0 nrest}, b = W_L^{nrest}, so a b^k = W_N^{nrest (k0 + RX k)}
+//   stage j = 2..S-1, key RX*LQ + sum_{2<=i<j} 16^{S-i} + nrest:
 //       a = 1, b = W_{L_j}^{nrest}, L_j = 16^{S-j+1}.
-// FP64 sincospi, each value rounded once to FP32.
+// Two parts: rows float4 (a, b), one per key, for the epilogues that advance
+// a b^k by packed multiplies (consecutive keys 16 bytes apart, as the lanes
+// of a contiguous chunk read them); then 8 float4 per key, entry
+// rows + 8 key + i = (Re w_{2i}, Re w_{2i+1}, Im w_{2i}, Im w_{2i+1}) with
+// w_k = a b^k, for the epilogues whose lanes share keys (loads then
+// broadcast).  Exponents reduced exactly in integers, FP64 sincospi, each
+// value rounded once to FP32.  One thread per entry.
 static __global__ void stage_twiddle_kernel(float4* out, int log2N, int rows) {
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= rows) return;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * kStageSlots) return;
+  const int row = idx < rows ? idx : (idx - rows) >> 3;
+  const int slot = idx < rows ? 0 : 1 + ((idx - rows) & 7);
   const int S = log2N / 4, RX = 1 << (log2N % 4), LQ = 1 << (4 * (S - 1));
-  double ae, an, be, bn;  // exponents e / denominators n of a and b
+  int64_t k0, nrest, n;  // stage 1: a b^k = W_n^{nrest (k0 + RX k)}; else W_n^{nrest k}
+  int64_t step;          // exponent step per output k: RX nrest (stage 1) or nrest
   if (row < RX * LQ) {
-    const int k0 = row / LQ, nrest = row % LQ;
-    ae = (double)(k0 * nrest);
-    an = (double)(RX * 16 * LQ);
-    be = (double)nrest;
-    bn = (double)(16 * LQ);
+    k0 = row / LQ;
+    nrest = row % LQ;
+    n = (int64_t)RX * 16 * LQ;
+    step = (int64_t)RX * nrest;
   } else {
     int j = 2, off = RX * LQ;
     while (j < S - 1 && row >= off + (1 << (4 * (S - j)))) {
       off += 1 << (4 * (S - j));
       ++j;
     }
-    ae = 0.0;
-    an = 1.0;
-    be = (double)(row - off);
-    bn = (double)(1 << (4 * (S - j + 1)));
+    k0 = 0;
+    nrest = row - off;
+    n = int64_t(1) << (4 * (S - j + 1));
+    step = nrest;
   }
-  double sa, ca, sb, cb;
-  sincospi(-2.0 * ae / an, &sa, &ca);
-  sincospi(-2.0 * be / bn, &sb, &cb);
-  out[row] = make_float4((float)ca, (float)sa, (float)cb, (float)sb);
+  const int64_t e_a = (k0 * nrest) % n;  // exponent of a (w_0)
+  double s0, c0, s1, c1;
+  if (slot == 0) {
+    sincospi(-2.0 * (double)e_a / (double)n, &s0, &c0);         // a
+    sincospi(-2.0 * (double)(step % n) / (double)n, &s1, &c1);  // b = W_n^{step}
+    out[idx] = make_float4((float)c0, (float)s0, (float)c1, (float)s1);
+    return;
+  }
+  const int i = slot - 1;
+  const int64_t e0 = (e_a + step * (2 * i)) % n, e1 = (e_a + step * (2 * i + 1)) % n;
+  sincospi(-2.0 * (double)e0 / (double)n, &s0, &c0);
+  sincospi(-2.0 * (double)e1 / (double)n, &s1, &c1);
+  out[idx] = make_float4((float)c0, (float)c1, (float)s0, (float)s1);
 }
 
 // B operands of the radix-16 stage: the real 32 x 32 form of a complex

@@ -206,11 +206,11 @@ struct tcfft_plan_s {
     if (S >= 2) rows = RX << (4 * (S - 1));
     for (int j = 2; j < S; ++j) rows += 1 << (4 * (S - j));
     float* t = nullptr;
-    const size_t bytes = (size_t)std::max(rows, 1) * 4 * sizeof(float);
+    const size_t bytes = (size_t)std::max(rows, 1) * kStageSlots * 4 * sizeof(float);
     if (cudaMalloc(&t, bytes) != cudaSuccess) return TCFFT_ERR_ALLOC;
     table_bytes += bytes;
     if (rows > 0) {
-      stage_twiddle_kernel<<<(rows + 255) / 256, 256>>>(reinterpret_cast<float4*>(t), log2N, rows);
+      stage_twiddle_kernel<<<(rows * kStageSlots + 255) / 256, 256>>>(reinterpret_cast<float4*>(t), log2N, rows);
       if (cudaGetLastError() != cudaSuccess) {
         cudaFree(t);
         return TCFFT_ERR_LAUNCH;

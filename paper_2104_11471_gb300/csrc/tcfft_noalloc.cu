@@ -99,8 +99,9 @@ tcfft_status setup_device(DeviceTables& d) {
   }
   for (int lg = tcfft::kMinLog2Pass; lg <= 12; ++lg) {
     const int rows = stage_rows(lg);
-    if (rows > 0)
-      tcfft::stage_twiddle_kernel<<<(rows + 255) / 256, 256>>>(d.stage + (size_t)lg * kStageSlot, lg, rows);
+    if (rows > 0)  // kStageSlots float4 per key: at most 272 * 9 = 2448 <= kStageSlot for lengths to 2^12
+      tcfft::stage_twiddle_kernel<<<(rows * tcfft::kStageSlots + 255) / 256, 256>>>(
+          d.stage + (size_t)lg * kStageSlot, lg, rows);
   }
   for (int r = 0; r < 4; ++r) tcfft::dft_b_kernel<<<1 << r, 1024>>>(d.dftb + (size_t)r * 16 * 1024, 1 << r);
   if (cudaGetLastError() != cudaSuccess) return TCFFT_ERR_LAUNCH;
